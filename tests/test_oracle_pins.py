@@ -1,0 +1,304 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties the oracle to something other than itself: values printed in the paper
+(tests/golden/), the combinatorial formula by brute force, closed forms of integer
+families, LAPACK through SciPy, algebraic invariants and the operation counts of
+Section 4.2.  A plausible slip in the oracle (a dropped term, a wrong sign or index, a
+transposed operand, the wrong triangle) fails at least one of them.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_2307_07611_gb300 import inputs
+from tests._golden import load, matrices
+
+
+# --- Section 3: Hopscotch series and the combinatorial theorem ----------------------
+
+def test_hopscotch_example_h15_order_and_lengths():
+    rows = load("hopscotch_H_1_5.txt")["H_1_5"]
+    printed = []
+    for r in rows:
+        seq, ln = r.split("|")
+        printed.append((tuple(int(v) for v in seq.split()), int(ln)))
+    got = oracle.hopscotch(1, 5)
+    assert [s for s, _ in printed] == got
+    assert [ln for _, ln in printed] == [len(s) for s in got]
+
+
+def test_hopscotch_translation_example():
+    blocks = load("hopscotch_translation.txt")
+    h14 = [tuple(int(v) for v in r.split()) for r in blocks["H_1_4"]]
+    h58 = [tuple(int(v) for v in r.split()) for r in blocks["H_5_8"]]
+    assert set(oracle.hopscotch(1, 4)) == set(h14)
+    assert set(oracle.hopscotch(5, 8)) == set(h58)
+    assert [tuple(v + 4 for v in s) for s in oracle.hopscotch(1, 4)] == oracle.hopscotch(5, 8)
+
+
+@pytest.mark.parametrize("a,b", [(1, 2), (1, 3), (2, 9), (3, 11), (1, 12)])
+def test_hopscotch_count_proposition(a, b):
+    seqs = oracle.hopscotch(a, b)
+    assert len(seqs) == 2 ** (b - a - 1)          # Proposition "corrTranlation"
+    assert len(set(seqs)) == len(seqs)
+    for s in seqs:
+        assert s[0] == a and s[-1] == b and list(s) == sorted(set(s))
+    assert oracle.hopscotch(a, a) == []
+
+
+def test_theorem_worked_example_exact():
+    g = matrices("theorem_example_4x4.txt")
+    t, tinv = g["T"], g["Tinv"]
+    assert np.array_equal(oracle.combinatorial_unit_upper(t), tinv)
+    assert np.array_equal(oracle.tri_inv(t, lower=False, unit=True), tinv)
+    assert np.array_equal(oracle.tri_inv(t, lower=False, unit=False), tinv)
+    # lower orientation by transposition (Section 2)
+    assert np.array_equal(oracle.tri_inv(t.T, lower=True, unit=True), tinv.T)
+    s, _, _ = oracle.crit_star(t)
+    assert np.array_equal(s, tinv)
+
+
+def test_theorem_n3_closed_form():
+    # S_13 = -T_13 + T_12 T_23 (proof of the main Theorem, n = 3)
+    t = np.array([[1.0, 0.3, -0.7], [0, 1, 1.9], [0, 0, 1]])
+    s = oracle.tri_inv(t, lower=False, unit=True)
+    assert s[0, 2] == pytest.approx(-t[0, 2] + t[0, 1] * t[1, 2], abs=1e-15)
+    assert s[0, 1] == -t[0, 1] and s[1, 2] == -t[1, 2]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("lower", [True, False])
+def test_oracle_matches_combinatorial_bruteforce(n, lower):
+    for seed in range(3):
+        t = inputs.tri_lower(n, seed=seed, law="uniform")
+        if not lower:
+            t = t.T.copy()
+        brute = oracle.combinatorial_tri_inv(t, lower=lower)
+        x = oracle.tri_inv(t, lower=lower)
+        scale = max(1.0, np.abs(brute).max())
+        assert np.abs(x - brute).max() <= 1e-14 * scale * n
+
+
+def test_oracle_unit_flag_ignores_stored_diagonal():
+    t = inputs.tri_lower(7, seed=4)
+    t_unit = t.copy()
+    np.fill_diagonal(t_unit, 1.0)
+    garbage = t.copy()
+    np.fill_diagonal(garbage, np.nan)
+    want = oracle.combinatorial_tri_inv(t_unit, lower=True)
+    got = oracle.tri_inv(garbage, lower=True, unit=True)
+    assert np.abs(got - want).max() < 1e-14
+
+
+def test_oracle_reads_only_its_triangle():
+    t = inputs.tri_lower(40, seed=2)
+    p = inputs.poison_upper(t)
+    assert np.array_equal(oracle.tri_inv(p, lower=True), oracle.tri_inv(t, lower=True))
+    pu = inputs.poison_upper(t).T.copy()
+    assert np.array_equal(oracle.tri_inv(pu, lower=False), oracle.tri_inv(t.T, lower=False))
+
+
+# --- Corollary "integer closure": exact integer families -----------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 17, 130])
+def test_all_ones_unit_lower_closed_form(n):
+    x = oracle.tri_inv(inputs.ones_unit_lower(n), lower=True, unit=True)
+    want = np.eye(n) - np.eye(n, k=-1)
+    assert np.array_equal(x, want)
+
+
+@pytest.mark.parametrize("vals", [(-1.0, 1.0), (-2.0, -1.0, 1.0, 2.0)])
+def test_bidiagonal_closed_form(vals):
+    n = 60 if len(vals) == 2 else 20
+    t, b = inputs.bidiagonal_unit_lower(n, seed=5, values=vals)
+    x = oracle.tri_inv(t, lower=True, unit=True)
+    want = np.zeros((n, n))
+    for j in range(n):
+        for i in range(j, n):
+            want[i, j] = (-1.0) ** (i - j) * np.prod(b[j:i])
+    assert np.array_equal(x, want)
+
+
+@pytest.mark.parametrize("n,half", [(64, 16), (200, 64), (257, 128)])
+def test_level_nilpotent_closed_form(n, half):
+    t, nmat = inputs.level_nilpotent_unit_lower(n, half, seed=3)
+    assert not np.any(nmat @ nmat)
+    x = oracle.tri_inv(t, lower=True, unit=True)
+    assert np.array_equal(x, np.eye(n) - nmat)
+
+
+def test_integer_product_family_exact():
+    n = 96
+    t1, n1 = inputs.level_nilpotent_unit_lower(n, 16, seed=1, lo=-1, hi=1)
+    t2, n2 = inputs.level_nilpotent_unit_lower(n, 32, seed=2, lo=-1, hi=1)
+    t = t1 @ t2
+    want = (np.eye(n) - n2) @ (np.eye(n) - n1)
+    x = oracle.tri_inv(t, lower=True, unit=True)
+    assert np.array_equal(x, want)
+    assert np.array_equal(x, np.round(x))
+
+
+# --- invariants and an independent library routine -----------------------------------
+
+def normwise_residual(t, x):
+    n = t.shape[0]
+    r = t @ x - np.eye(n)
+    return np.linalg.norm(r) / (np.linalg.norm(t) * np.linalg.norm(x))
+
+
+@pytest.mark.parametrize("lower", [True, False])
+def test_invariants_config_law_n512(lower):
+    t = inputs.tri_lower(512, seed=0, law="uniform")
+    if not lower:
+        t = t.T.copy()
+    x = oracle.tri_inv(t, lower=lower)
+    assert normwise_residual(t, x) <= 1e-13
+    other = np.triu(x, 1) if lower else np.tril(x, -1)
+    assert not np.any(other)
+    assert np.array_equal(np.diag(x), 1.0 / np.diag(t))
+
+
+def test_block_identity():
+    n, h = 300, 128
+    t = inputs.tri_lower(n, seed=1, law="normal")
+    x = oracle.tri_inv(t)
+    xa = oracle.tri_inv(t[:h, :h])
+    xc = oracle.tri_inv(t[h:, h:])
+    assert np.abs(x[:h, :h] - xa).max() < 1e-14
+    assert np.abs(x[h:, h:] - xc).max() < 1e-14
+    x21 = -xc @ t[h:, :h] @ xa
+    assert np.abs(x[h:, :h] - x21).max() < 1e-13 * max(1, np.abs(x21).max())
+
+
+@pytest.mark.parametrize("n", [33, 257])
+@pytest.mark.parametrize("lower", [True, False])
+@pytest.mark.parametrize("unit", [False, True])
+def test_matches_lapack_trtrs(n, lower, unit):
+    t = inputs.tri_lower(n, seed=n, law="normal")
+    if not lower:
+        t = t.T.copy()
+    want = sla.solve_triangular(t, np.eye(n), lower=lower, unit_diagonal=unit)
+    got = oracle.tri_inv(t, lower=lower, unit=unit)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_selected_columns_equal_full():
+    n = 150
+    t = inputs.tri_lower(n, seed=9, law="normal")
+    cols = [0, 1, 77, 148, 149]
+    full = oracle.tri_inv(t)
+    assert np.array_equal(oracle.tri_inv_cols(t, cols), full[:, cols])
+    fullu = oracle.tri_inv(t.T, lower=False)
+    assert np.array_equal(oracle.tri_inv_cols(t.T, cols, lower=False), fullu[cols, :].T)
+
+
+def test_singular_pivot_reported():
+    t = inputs.tri_lower(20, seed=1)
+    t[7, 7] = 0.0
+    t[12, 12] = np.inf
+    with pytest.raises(oracle.SingularError) as e:
+        oracle.tri_inv(t)
+    assert e.value.index == 7
+    x = oracle.tri_inv(t, unit=True)  # diagonal not read
+    assert np.isfinite(x).all()
+
+
+# --- Section 4.2: CRIT* operation counts ---------------------------------------------
+
+@pytest.mark.parametrize("n", list(range(2, 26)))
+def test_crit_star_counts_match_paper(n):
+    t = np.triu(np.random.default_rng(n).uniform(-1, 1, (n, n)), 1) + np.eye(n)
+    s, mults, adds = oracle.crit_star(t)
+    assert mults == n * (n - 1) * (n - 2) // 6            # Eq. "phimult"
+    assert adds == (n - 1) * (n - 2) * (n - 3) // 6       # Eq. "phiaddsub"
+    # I_T^CRIT(m) = m(m+1)/2 + phi_x + phi_pm = (m^3 - 3m^2 + 8m - 3)/3
+    assert 3 * (n * (n + 1) // 2 + mults + adds) == n ** 3 - 3 * n ** 2 + 8 * n - 3
+    assert np.abs(s - oracle.tri_inv(t, lower=False, unit=True)).max() < 1e-12
+
+
+def test_crit_total_flops_small_values():
+    f = lambda m: (m ** 3 - 3 * m ** 2 + 8 * m - 3) // 3
+    assert f(3) == 7 and f(4) == 15
+
+
+# --- Section 5 / 6.1: Crout (SKUL) factors and the general inverse ------------------
+
+def test_skul_printed_factors():
+    g = matrices("skul_sqr_5x5.txt")
+    lo, up = oracle.crout(g["A"])
+    assert np.abs(lo - g["L"]).max() < 1.5e-4
+    assert np.abs(up - g["U"]).max() < 1.5e-4
+    assert np.abs(oracle.tri_inv(up, lower=False, unit=True) - g["S"]).max() < 1.5e-4
+    assert np.abs(oracle.tri_inv(lo, lower=True) - g["K"]).max() < 1.5e-4
+    # A^-1 = S K
+    assert np.abs(oracle.gen_inv(g["A"]) - g["S"] @ g["K"]).max() < 2e-4
+
+
+def test_sqr_printed_r_inverse():
+    g = matrices("skul_sqr_5x5.txt")
+    assert np.abs(oracle.tri_inv(g["R"], lower=False) - g["S_R"]).max() < 1.5e-4
+
+
+@pytest.mark.parametrize("n", [1, 7, 120])
+def test_gen_inv_matches_lapack(n):
+    a = inputs.general(n, seed=n, dtype=np.float64)
+    lo, up = oracle.crout(a)
+    assert np.abs(lo @ up - a).max() < 1e-13
+    assert not np.any(np.triu(lo, 1)) and not np.any(np.tril(up, -1))
+    assert np.array_equal(np.diag(up), np.ones(n))
+    x = oracle.gen_inv(a)
+    want = np.linalg.inv(a)
+    assert np.abs(x - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_gen_inv_singular_leading_block():
+    a = inputs.general(6, seed=1, dtype=np.float64)
+    a[0, 0] = 0.0
+    with pytest.raises(oracle.SingularError) as e:
+        oracle.gen_inv(a)
+    assert e.value.index == 0
+
+
+# --- adjoint: dT = -P(X^T G X^T) ------------------------------------------------------
+
+def _loss(t, w, lower, unit):
+    x = sla.solve_triangular(t, np.eye(t.shape[0]), lower=lower, unit_diagonal=unit)
+    return float(np.sum(w * x))
+
+
+@pytest.mark.parametrize("lower,unit,n", [(True, False, 32), (False, False, 16), (True, True, 16)])
+def test_tri_grad_central_differences(lower, unit, n):
+    t = inputs.tri_lower(n, seed=11, law="uniform")
+    if not lower:
+        t = t.T.copy()
+    w = np.random.default_rng(12).standard_normal((n, n))
+    x = sla.solve_triangular(t, np.eye(n), lower=lower, unit_diagonal=unit)
+    got = oracle.tri_grad(x, w, lower=lower, unit=unit)
+    fd = np.zeros((n, n))
+    for i, j in itertools.product(range(n), range(n)):
+        free = (i >= j) if lower else (i <= j)
+        if unit and i == j:
+            free = False
+        if not free:
+            continue
+        h = 1e-6 * max(1.0, abs(t[i, j]))
+        tp, tm = t.copy(), t.copy()
+        tp[i, j] += h
+        tm[i, j] -= h
+        fd[i, j] = (_loss(tp, w, lower, unit) - _loss(tm, w, lower, unit)) / (2 * h)
+    assert np.linalg.norm(got - fd) <= 1e-7 * np.linalg.norm(fd)
+    outside = np.triu(got, 1) if lower else np.tril(got, -1)
+    assert not np.any(outside)
+
+
+def test_tri_grad_ignores_other_triangle_of_g():
+    n = 24
+    t = inputs.tri_lower(n, seed=2)
+    x = oracle.tri_inv(t)
+    g = np.random.default_rng(3).standard_normal((n, n))
+    g2 = g.copy()
+    g2[np.triu_indices(n, 1)] = 1e3
+    assert np.abs(oracle.tri_grad(x, g) - oracle.tri_grad(x, g2)).max() < 1e-9
