@@ -1,0 +1,379 @@
+"""Benchmark: triangular-inverse TFLOP/s (n^3/3 flops) at n = 8192, mixed vs plain FP32.
+
+One step = one in-place inverse of a lower-triangular FP32 n = 8192 matrix (diag
+U[1,2], strict lower N(0,1)/sqrt(n), seed 0) through the library's C ABI: leaf
+recurrence, every split level's two products and, in mixed mode, the Newton-Schulz
+step.  Before each step the pristine T is restored by an untimed device copy; each step
+is timed with CUDA events on the launching stream (inputs are 268 MB, larger than the
+129 MB L2).  Under torchrun every rank inverts its own replica (no collective: a single
+inverse does not shard at this size); value = all ranks' flops / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode mixed|plain]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tri-inverse TFLOP/s (n^3/3) at n=8192, mixed vs plain FP32, equal residual"
+WORKLOAD = ("lower-triangular FP32 n=8192: diag U[1,2], strict-lower N(0,1)/sqrt(n), seed 0")
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="auto", choices=["auto", "mixed", "plain"])
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-quality", action="store_true",
+                   help="skip the residual / oracle check (for profiler launch lists)")
+    p.add_argument("--cpu-sample-stride", type=int, default=1)
+    return p.parse_args()
+
+
+def flops_tri(n: int) -> float:
+    return n ** 3 / 3.0
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+# ---- CPU oracle timing (reference arm and cpu_baseline) ------------------------------
+
+_T_CACHE = {}
+
+
+def oracle_sample(n: int, stride: int, offset: int = 0):
+    """Time the FP64 oracle's column recurrence on every `stride`-th column of the
+    workload; returns (TFLOP/s in the n^3/3 convention, seconds, threads, sample text).
+    The sample's share of the n^3/3 work is sum_j (n-j)(n-j-1) over the sampled j."""
+    import numpy as np
+    import oracle
+    from paper_2307_07611_gb300 import inputs
+
+    if n not in _T_CACHE:
+        _T_CACHE[n] = inputs.tri_lower(n, seed=0, law="normal", dtype=np.float32).astype(np.float64)
+    t = _T_CACHE[n]
+    cols = np.arange(offset % stride, n, stride, dtype=np.int64)
+    w_all = sum((n - j) * (n - j - 1) for j in range(n))
+    w_s = float(sum((n - int(j)) * (n - int(j) - 1) for j in cols))
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.tri_inv_cols(t, cols, lower=True, threads=threads)
+    dt = time.perf_counter() - t0
+    work = flops_tri(n) * w_s / w_all
+    return work / dt / 1e12, dt, threads, f"{len(cols)} of {n} columns (every {stride}th), {w_s / w_all:.3f} of the work"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times, vals = [], []
+    stride = 32
+    for i in range(args.warmup + args.steps):
+        v, dt, threads, sample = oracle_sample(args.n, stride, offset=i)
+        if i >= args.warmup:
+            times.append(dt)
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": args.n, "mode": "fp64 cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": "per step: " + sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- clocks ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(", ") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- our arm ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_07611_gb300 import inputs, lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib.load()
+
+    mode = args.mode
+    if mode == "auto":
+        mode = "mixed" if getattr(lib, "MIXED_AVAILABLE", False) else "plain"
+    n = args.n
+    code = lib.TRI_F32_MIXED if mode == "mixed" else lib.TRI_F32
+
+    # Column-major lower T == row-major tensor holding T^T.
+    t_host = inputs.tri_lower(n, seed=0, law="normal", dtype=np.float32)
+    t_cm = torch.from_numpy(np.ascontiguousarray(t_host.T))
+    pristine = t_cm.to(dev)
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+    sh = int(stream.cuda_stream)
+    ws_bytes = lib.tri_inv_workspace_size(n, code)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+
+    def step(code_):
+        work.copy_(pristine)                     # untimed restore (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = lib.tri_inv_ex(lib.TRI_LOWER, lib.TRI_NONUNIT, n, work.data_ptr(), n, code_,
+                            ws_ptr, ws_bytes, sh)
+        e1.record(stream)
+        lib.check(st, "tri_inv_ex")
+        return e0, e1
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(code_, steps, warmup, trace=False):
+        for _ in range(warmup):
+            step(code_)
+        barrier()
+        if trace:
+            lib.tri_trace_enable(True)
+        evs = [step(code_) for _ in range(steps)]
+        barrier()
+        rep = None
+        if trace:
+            rep = lib.tri_trace_report()
+            lib.tri_trace_enable(False)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return sum(ms), ms, rep
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)  # let nvidia-smi start sampling before the timed region
+    total_ms, per_ms, trace = timed(code, args.steps, args.warmup, trace=True)
+    clk = clocks.stop()
+
+    # max over ranks
+    tot = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms = float(tot.item())
+    ms_per_step = total_ms / args.steps
+    value = world * flops_tri(n) * args.steps / (total_ms * 1e-3) / 1e12
+
+    # quality of this mode's result (outside the timed region)
+    def quality(code_):
+        step(code_)
+        torch.cuda.synchronize()
+        st, bad = lib.tri_get_info(sh)
+        x = work.clone()            # column-major X: row-major X^T
+        t = pristine
+        # normwise residual in FP64 (torch on the device, measurement only)
+        xd = x.double().T.tril()
+        td = t.double().T.tril()
+        r = td @ xd
+        r.diagonal().sub_(1.0)
+        resid = float(r.norm() / (td.norm() * xd.norm()))
+        cols = [0, 1, 4095, 4096, n - 1]
+        err = None
+        if rank == 0:
+            import oracle
+            want = oracle.tri_inv_cols(t_host.astype(np.float64), cols, lower=True)
+            got = xd[:, cols].cpu().numpy()
+            err = float(np.abs(got - want).max() / np.abs(want).max())
+        return resid, err, st
+
+    resid = err = st_info = None
+    if not args.no_quality:
+        resid, err, st_info = quality(code)
+    extra = {}
+    if mode == "mixed":
+        p_total, _, _ = timed(lib.TRI_F32, max(3, args.steps // 2), 2)
+        p_resid = p_err = None
+        if not args.no_quality:
+            p_resid, p_err, _ = quality(lib.TRI_F32)
+        extra["plain_fp32"] = {
+            "value": flops_tri(n) * max(3, args.steps // 2) / (p_total * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "ms_per_step": p_total / max(3, args.steps // 2),
+            "residual": p_resid, "max_rel_err_vs_oracle_cols": p_err}
+
+    # roofline of the dominant kernel (largest share of traced device time)
+    peaks, peak_src = load_peaks()
+    roof = None
+    if trace:
+        top = max(trace.items(), key=lambda kv: kv[1]["ms"])
+        name, rec = top
+        if "tc" in name or "bf16" in name:
+            bound, unit = "tensor", "TFLOP/s"
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
+        else:
+            bound, unit = "alu", "TFLOP/s"
+            props = torch.cuda.get_device_properties(dev)
+            mhz = float(peaks.get("sm_max_mhz", 2070.0))
+            fma_per_clk = 128 if "f32" in name else 2
+            peak = props.multi_processor_count * fma_per_clk * 2 * mhz * 1e6 / 1e12
+            achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
+        roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"{peak_src} bf16_tflops_sustained" if bound == "tensor"
+                                else f"derived: SMs x {fma_per_clk} FMA/clk x 2 x {mhz:.0f} MHz"),
+                "share_of_step": rec["ms"] / total_ms}
+    launches = sum(v["launches"] for v in trace.values()) if trace else None
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = t_cm.pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        dev_buf = torch.empty_like(pristine)
+        k = max(3, args.steps // 2)
+
+        def e2e_step():
+            dev_buf.copy_(h_in, non_blocking=True)
+            lib.check(lib.tri_inv(lib.TRI_LOWER, lib.TRI_NONUNIT, n, dev_buf.data_ptr(), n, code, sh))
+            h_out.copy_(dev_buf, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        nbytes = t_cm.numel() * 4
+        e2e = {"value": world * flops_tri(n) * k / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": ms / k}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, threads, sample = oracle_sample(n, args.cpu_sample_stride)
+        cpu = {"value": v, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": sample, "seconds": dt}
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3-split, f32 accumulate" if mode == "mixed" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "mode": mode, "leaf": 64,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (268 MB per matrix)",
+                       "restore": "untimed device copy of T before each step"},
+            "residual": resid, "max_rel_err_vs_oracle_cols": err,
+            "info_status": st_info,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "per_step_ms_min": min(per_ms), "per_step_ms_median": statistics.median(per_ms),
+            "trace": trace,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

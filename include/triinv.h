@@ -1,0 +1,127 @@
+/*
+ * triinv.h -- C ABI of the GB300 (sm_103a) triangular-inversion library.
+ *
+ * The library inverts a non-singular triangular matrix T by the recursive triangular
+ * split of arXiv 2307.07611 (COMBRIT with block count 2, Section 4.1, Algorithm
+ * "COMBRIT"; the block inverse of the proof of the main Theorem, Section 3):
+ *
+ *     T = [A 0; B C]   ->   T^-1 = [A^-1 0; -C^-1 B A^-1  C^-1]
+ *
+ * The diagonal leaf blocks are inverted by the column recurrence of CRIT (Section 4.2,
+ * Algorithm "CRIT", transposed to lower form):
+ *     x_jj = 1/t_jj,   x_ij = -(1/t_ii) * sum_{k=j}^{i-1} t_ik x_kj   (i > j)
+ * and the off-diagonal blocks by two dense products per split (Section 4.1, Eq.
+ * "ptfm" counts one of them as m^3 flops).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are COLUMN-MAJOR: element (i, j) of a matrix with leading dimension ld
+ *     is ptr[i + j*ld].  Pointers passed as `void*` data are DEVICE pointers unless a
+ *     comment says "host".
+ *   - Only the triangle named by `uplo` is read and written (LAPACK trtri semantics);
+ *     the other triangle is never touched.  With TRI_UNIT the diagonal is taken as 1
+ *     and neither read nor written.
+ *   - `stream` is a cudaStream_t passed as `void*`; NULL is the legacy default stream.
+ *     Every call is asynchronous on `stream`: a returned TRI_OK means the work was
+ *     queued (argument errors are detected and returned before anything is queued).
+ *   - The caller owns all memory it passes.  The library never frees caller memory.
+ *     Internal scratch comes from the `_ex` workspace argument or, in the plain entry
+ *     points, from CUDA's stream-ordered allocator (TRI_ERR_NOMEM if that fails).
+ *   - A zero or non-finite pivot (t_ii, or a pivot of the LU in gen_inv) does not stop
+ *     the queued work; its index is recorded on the device (smallest index wins) and
+ *     reported by tri_get_info().  The result is then unspecified.  No pivoting is done
+ *     and there is no small-pivot threshold.
+ *   - Every wait inside a kernel is bounded; a wait that runs out records
+ *     TRI_ERR_TIMEOUT, reported by tri_get_info().
+ */
+#ifndef TRIINV_H
+#define TRIINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TRI_API __attribute__((visibility("default")))
+#else
+#define TRI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TRI_OK = 0,
+    TRI_ERR_ARG = 1,         /* invalid argument (nothing was queued)                    */
+    TRI_ERR_SINGULAR = 2,    /* zero or non-finite pivot (from tri_get_info)             */
+    TRI_ERR_NOMEM = 3,       /* scratch allocation failed / workspace too small          */
+    TRI_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed              */
+    TRI_ERR_TIMEOUT = 5,     /* a bounded device wait ran out (from tri_get_info)        */
+    TRI_ERR_UNSUPPORTED = 6  /* valid request this build does not provide                */
+} tri_status;
+
+typedef enum { TRI_LOWER = 0, TRI_UPPER = 1 } tri_uplo;
+typedef enum { TRI_NONUNIT = 0, TRI_UNIT = 1 } tri_diag;
+
+typedef enum {
+    TRI_F64 = 0,       /* FP64 storage, FP64 leaf recurrence and DFMA products            */
+    TRI_F32 = 1,       /* FP32 storage, FP32 leaf recurrence and FFMA products ("plain")  */
+    TRI_F32_MIXED = 2  /* FP32 storage; split-BF16 tensor-core products with FP32
+                          accumulation, then one Newton-Schulz step X <- X + X(I - TX)    */
+} tri_dtype;
+
+/* Human-readable name of a status code (static string, never NULL). */
+TRI_API const char *tri_status_string(tri_status s);
+
+/* Library version string, e.g. "0.1.0 sm_103a". */
+TRI_API const char *tri_version(void);
+
+/* ---------------------------------------------------------------------------------
+ * Single triangular inverse, in place: A <- A^-1 on the `uplo` triangle.
+ *   uplo  TRI_LOWER: A is lower triangular; TRI_UPPER: upper (handled as the transpose
+ *         of a lower matrix, Section 2 of the paper).
+ *   diag  TRI_UNIT: unit diagonal, not referenced.
+ *   n     order, n >= 0 (n == 0 is a no-op).
+ *   a     device pointer to an lda x n column-major matrix (FP64 for TRI_F64, FP32
+ *         otherwise).
+ *   lda   leading dimension, lda >= max(1, n).
+ * Errors: TRI_ERR_ARG for bad enums, n < 0, lda < max(1,n) or a == NULL with n > 0;
+ *         TRI_ERR_NOMEM if scratch cannot be allocated; TRI_ERR_CUDA on a launch error.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                   tri_dtype dtype, void *stream);
+
+/* Bytes of scratch tri_inv_ex needs for order n (0 if none).  Scratch must be
+ * 256-byte aligned device memory and must not be used by anything else until the
+ * queued work completes. */
+TRI_API size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype);
+
+/* tri_inv with caller-provided scratch.  TRI_ERR_NOMEM if ws_bytes is smaller than
+ * tri_inv_workspace_size(n, dtype) or `workspace` is not 256-byte aligned. */
+TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                      tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream`, then reports and clears the device-side status of the calling
+ * thread's current device: TRI_ERR_SINGULAR with *first_bad_index set to the smallest
+ * bad pivot index recorded since the last call, TRI_ERR_TIMEOUT if a bounded wait ran
+ * out, otherwise TRI_OK with *first_bad_index = -1.  first_bad_index is a host pointer
+ * and may be NULL. */
+TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
+
+/* ---------------------------------------------------------------------------------
+ * Kernel tracing (host-side bookkeeping, off by default).  While enabled, every kernel
+ * the library launches is bracketed by CUDA events on its own stream, and the
+ * algorithmic flops / bytes of that launch are recorded.
+ *   tri_trace_enable(1) clears earlier records and starts recording; (0) stops.
+ *   tri_trace_report() synchronises on the recorded events and writes a JSON object
+ *   {"<kernel>": {"launches": L, "ms": T, "flops": F, "bytes": B}, ...} into the host
+ *   buffer `buf` of `cap` bytes (NUL-terminated, truncated if too small).  Returns the
+ *   length the full report needs (excluding the NUL), or -1 on a CUDA error.
+ * --------------------------------------------------------------------------------- */
+TRI_API void tri_trace_enable(int on);
+TRI_API int64_t tri_trace_report(char *buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRIINV_H */

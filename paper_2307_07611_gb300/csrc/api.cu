@@ -1,0 +1,289 @@
+// api.cu -- the C ABI (include/triinv.h): argument checks, per-device status words,
+// scratch handling, kernel tracing and the level scheduler of the recursive split.
+//
+// Recursive triangular split (Section 4.1, Algorithm "COMBRIT" with two blocks; block
+// inverse from the proof of the main Theorem, Section 3):
+//     T = [A 0; B C]  ->  T^-1 = [A^-1 0; -C^-1 B A^-1  C^-1].
+// The recursion tree is walked bottom-up by levels.  The matrix is logically padded with
+// identity up to leaf * 2^L (the paper pads with canonical-basis columns, Appendix), so
+// every level has the same half-size h = leaf * 2^(s-1) and pairs start at multiples of
+// 2h; padded rows and columns are never touched (the kernels clip them).
+//   level 0: every leaf block is inverted by the CRIT column recurrence (leaf.cu);
+//   level s: for every pair, W = B X_A then B <- -X_C W (trmm_simt.cu / tc_gemm.cu).
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace triinv {
+
+// Device status words: the smallest bad pivot index seen and the timeout flag.  One copy
+// per device (module globals are per context); host code reaches them through
+// cudaGetSymbolAddress.
+__device__ long long g_info_word = LLONG_MAX;
+__device__ int g_timeout_word = 0;
+
+namespace {
+
+struct DeviceState {
+    bool ready = false;
+    long long *info = nullptr;
+    int *timeout = nullptr;
+    int sm_count = 0;
+};
+
+std::mutex g_mu;
+DeviceState g_dev[64];
+
+tri_status device_ctx(cudaStream_t stream, Ctx *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TRI_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.ready) {
+        void *pi = nullptr, *pt = nullptr;
+        if (cudaGetSymbolAddress(&pi, g_info_word) != cudaSuccess) return TRI_ERR_CUDA;
+        if (cudaGetSymbolAddress(&pt, g_timeout_word) != cudaSuccess) return TRI_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return TRI_ERR_CUDA;
+        // Keep freed stream-ordered allocations cached in the pool instead of returning
+        // them to the driver, so repeated calls do not pay for fresh allocations.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        d.info = (long long *)pi;
+        d.timeout = (int *)pt;
+        d.ready = true;
+    }
+    out->stream = stream;
+    out->info = d.info;
+    out->timeout = d.timeout;
+    out->sm_count = d.sm_count;
+    out->device = dev;
+    return TRI_OK;
+}
+
+// ---- tracing -------------------------------------------------------------------------
+struct TraceRec {
+    std::string kernel;
+    cudaEvent_t beg, end;
+    double flops, bytes;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void clear_trace_locked() {
+    for (auto &r : g_trace) {
+        g_event_pool.push_back(r.beg);
+        g_event_pool.push_back(r.end);
+    }
+    g_trace.clear();
+}
+
+}  // namespace
+
+TraceScope::TraceScope(cudaStream_t stream, const char *kernel, double flops, double bytes)
+    : slot(-1), stream_(stream) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (!g_trace_on) return;
+    TraceRec r{kernel, take_event(), take_event(), flops, bytes};
+    if (!r.beg || !r.end) return;
+    cudaEventRecord(r.beg, stream);
+    g_trace.push_back(r);
+    slot = (int)g_trace.size() - 1;
+}
+
+TraceScope::~TraceScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (slot < (int)g_trace.size()) cudaEventRecord(g_trace[slot].end, stream_);
+}
+
+// ---- plans ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kLeafPlain = 64;
+
+size_t elem_size(tri_dtype dt) { return dt == TRI_F64 ? 8 : 4; }
+
+// Largest per-level scratch of the plain path: one h x h W block per active pair.
+size_t plain_ws_bytes(int64_t n, tri_dtype dt) {
+    size_t best = 0;
+    for (int64_t h = kLeafPlain; h < n; h *= 2) {
+        const int64_t p = level_pairs(n, h);
+        best = std::max(best, (size_t)p * (size_t)h * (size_t)h * elem_size(dt));
+    }
+    return best;
+}
+
+bool valid_enums(tri_uplo u, tri_diag d, tri_dtype t) {
+    return (u == TRI_LOWER || u == TRI_UPPER) && (d == TRI_NONUNIT || d == TRI_UNIT) &&
+           (t == TRI_F64 || t == TRI_F32 || t == TRI_F32_MIXED);
+}
+
+tri_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA; }
+
+tri_status run_plain(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
+                     int64_t lda, void *ws) {
+    cudaError_t e = launch_leaf(c, dt, trans, unit, n, a, lda, kLeafPlain);
+    if (e != cudaSuccess) return TRI_ERR_CUDA;
+    for (int64_t h = kLeafPlain; h < n; h *= 2) {
+        e = launch_trmm_level(c, dt, trans, unit, 0, n, a, lda, h, ws);
+        if (e != cudaSuccess) return TRI_ERR_CUDA;
+        e = launch_trmm_level(c, dt, trans, unit, 1, n, a, lda, h, ws);
+        if (e != cudaSuccess) return TRI_ERR_CUDA;
+    }
+    return TRI_OK;
+}
+
+}  // namespace
+}  // namespace triinv
+
+using namespace triinv;
+
+extern "C" {
+
+const char *tri_status_string(tri_status s) {
+    switch (s) {
+        case TRI_OK: return "TRI_OK";
+        case TRI_ERR_ARG: return "TRI_ERR_ARG: invalid argument";
+        case TRI_ERR_SINGULAR: return "TRI_ERR_SINGULAR: zero or non-finite pivot";
+        case TRI_ERR_NOMEM: return "TRI_ERR_NOMEM: scratch allocation failed or workspace too small";
+        case TRI_ERR_CUDA: return "TRI_ERR_CUDA: CUDA runtime or launch error";
+        case TRI_ERR_TIMEOUT: return "TRI_ERR_TIMEOUT: a bounded device wait ran out";
+        case TRI_ERR_UNSUPPORTED: return "TRI_ERR_UNSUPPORTED: not provided by this build";
+    }
+    return "unknown tri_status";
+}
+
+const char *tri_version(void) { return "0.1.0 sm_103a"; }
+
+size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype) {
+    if (n <= 0) return 0;
+    if (dtype == TRI_F64 || dtype == TRI_F32) return plain_ws_bytes(n, dtype);
+    return 0;
+}
+
+tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                      tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream) {
+    if (!valid_enums(uplo, diag, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    if (dtype == TRI_F32_MIXED) return TRI_ERR_UNSUPPORTED;
+    const size_t need = tri_inv_workspace_size(n, dtype);
+    if (need > 0 && (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)))
+        return TRI_ERR_NOMEM;
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    return run_plain(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, workspace);
+}
+
+tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                   tri_dtype dtype, void *stream) {
+    if (!valid_enums(uplo, diag, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    const size_t need = tri_inv_workspace_size(n, dtype);
+    void *ws = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (need > 0) {
+        Ctx c;
+        tri_status st = device_ctx(s, &c);  // sets the pool's release threshold once
+        if (st != TRI_OK) return st;
+        if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+            cudaGetLastError();
+            return TRI_ERR_NOMEM;
+        }
+    }
+    tri_status st = tri_inv_ex(uplo, diag, n, a, lda, dtype, ws, need, stream);
+    if (ws) {
+        cudaError_t e = cudaFreeAsync(ws, s);
+        if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
+    }
+    return st;
+}
+
+tri_status tri_get_info(void *stream, int64_t *first_bad_index) {
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TRI_ERR_CUDA;
+    long long info = LLONG_MAX;
+    int tmo = 0;
+    if (cudaMemcpy(&info, c.info, sizeof(info), cudaMemcpyDeviceToHost) != cudaSuccess) return TRI_ERR_CUDA;
+    if (cudaMemcpy(&tmo, c.timeout, sizeof(tmo), cudaMemcpyDeviceToHost) != cudaSuccess) return TRI_ERR_CUDA;
+    const long long none = LLONG_MAX;
+    const int zero = 0;
+    if (cudaMemcpy(c.info, &none, sizeof(none), cudaMemcpyHostToDevice) != cudaSuccess) return TRI_ERR_CUDA;
+    if (cudaMemcpy(c.timeout, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess) return TRI_ERR_CUDA;
+    if (first_bad_index) *first_bad_index = (info == LLONG_MAX) ? -1 : (int64_t)info;
+    if (tmo) return TRI_ERR_TIMEOUT;
+    if (info != LLONG_MAX) return TRI_ERR_SINGULAR;
+    return TRI_OK;
+}
+
+void tri_trace_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (on) clear_trace_locked();
+    g_trace_on = on != 0;
+}
+
+int64_t tri_trace_report(char *buf, size_t cap) {
+    struct Agg { std::string k; int64_t launches; double ms, flops, bytes; };
+    std::vector<Agg> agg;
+    {
+        std::lock_guard<std::mutex> lk(g_trace_mu);
+        for (auto &r : g_trace) {
+            if (cudaEventSynchronize(r.end) != cudaSuccess) return -1;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.beg, r.end) != cudaSuccess) return -1;
+            auto it = std::find_if(agg.begin(), agg.end(), [&](const Agg &a) { return a.k == r.kernel; });
+            if (it == agg.end()) {
+                agg.push_back({r.kernel, 0, 0.0, 0.0, 0.0});
+                it = agg.end() - 1;
+            }
+            it->launches += 1;
+            it->ms += ms;
+            it->flops += r.flops;
+            it->bytes += r.bytes;
+        }
+    }
+    std::string out = "{";
+    for (size_t i = 0; i < agg.size(); ++i) {
+        char tmp[512];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e, \"bytes\": %.6e}",
+                 i ? ", " : "", agg[i].k.c_str(), (long long)agg[i].launches, agg[i].ms, agg[i].flops,
+                 agg[i].bytes);
+        out += tmp;
+    }
+    out += "}";
+    if (buf && cap) {
+        size_t m = std::min(cap - 1, out.size());
+        memcpy(buf, out.data(), m);
+        buf[m] = 0;
+    }
+    return (int64_t)out.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// internal.cuh -- declarations shared by the library's translation units.
+// Not part of the public ABI (include/triinv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "triinv.h"
+
+namespace triinv {
+
+// Per-call launch context.
+struct Ctx {
+    cudaStream_t stream;
+    long long *info;   // device: smallest bad pivot index seen (LLONG_MAX = none)
+    int *timeout;      // device: set to 1 when a bounded wait runs out
+    int sm_count;
+    int device;
+};
+
+// Lower-orientation view of a column-major matrix.  For an upper-triangular matrix U
+// stored column-major, the lower view is U^T, i.e. element (i, j) of the view lives at
+// p[j + i*ld] (trans == true).  Section 2 of the paper: the lower case is the transpose
+// of the upper one.
+template <bool TRANS>
+__host__ __device__ __forceinline__ int64_t vidx(int64_t i, int64_t j, int64_t ld) {
+    return TRANS ? (j + i * ld) : (i + j * ld);
+}
+
+// ---- tracing (api.cu) -------------------------------------------------------------
+// While tracing is on, TraceScope records a CUDA event pair around the launches made in
+// its lifetime on `stream`, and books the launch's algorithmic flops and bytes.
+struct TraceScope {
+    int slot;
+    TraceScope(cudaStream_t stream, const char *kernel, double flops, double bytes);
+    ~TraceScope();
+    cudaStream_t stream_;
+};
+
+// ---- leaf inverse (leaf.cu) -------------------------------------------------------
+// Inverts every diagonal block [q*leaf, min(q*leaf+leaf, n)) of the lower view in place
+// by the column recurrence.  leaf must be 16, 32 or 64.
+cudaError_t launch_leaf(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n,
+                        void *a, int64_t lda, int leaf);
+
+// ---- SIMT level products (trmm_simt.cu) -------------------------------------------
+// One split level with half-size h: for every active pair q (A-block at q*2h, C-block
+// at q*2h+h, clipped to n):
+//   mode 0:  W_q = B_q * X_A        (B_q: rows of C x cols of A; X_A lower)
+//   mode 1:  B_q <- -X_C * W_q      (X_C lower)
+// W is column-major with leading dimension h, pair q at offset q*h*h.
+cudaError_t launch_trmm_level(const Ctx &c, tri_dtype dt, bool trans, bool unit, int mode,
+                              int64_t n, void *a, int64_t lda, int64_t h, void *w);
+
+// Number of active pairs at split half-size h.
+inline int64_t level_pairs(int64_t n, int64_t h) {
+    return n > h ? (n - h + 2 * h - 1) / (2 * h) : 0;
+}
+
+}  // namespace triinv

@@ -1,0 +1,173 @@
+"""Thin ctypes binding of libtriinv.so (include/triinv.h), plus torch-tensor helpers.
+
+The functions named like the C entry points (``tri_inv``, ``tri_inv_ex``, ...) only
+marshal arguments: every step of the computation runs in the library's CUDA kernels.
+Loading fails loudly (``RuntimeError``) if the library has not been built; there is no
+CPU fallback.
+
+The torch helpers (``inv``, ...) map a row-major torch tensor onto the column-major
+ABI: a C-contiguous lower-triangular n x n tensor is, column-major, an upper-triangular
+matrix with lda = stride(0), so the helper flips ``uplo`` instead of copying.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(PKG, "_build", "libtriinv.so")
+
+TRI_OK, TRI_ERR_ARG, TRI_ERR_SINGULAR, TRI_ERR_NOMEM, TRI_ERR_CUDA, TRI_ERR_TIMEOUT, \
+    TRI_ERR_UNSUPPORTED = range(7)
+TRI_LOWER, TRI_UPPER = 0, 1
+TRI_NONUNIT, TRI_UNIT = 0, 1
+TRI_F64, TRI_F32, TRI_F32_MIXED = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TriError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {status_string(status)}" if what else status_string(status))
+
+
+def _declare(lib):
+    i64, i32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    sigs = {
+        "tri_status_string": ([i32], ctypes.c_char_p),
+        "tri_version": ([], ctypes.c_char_p),
+        "tri_inv": ([i32, i32, i64, vp, i64, i32, vp], i32),
+        "tri_inv_workspace_size": ([i64, i32], sz),
+        "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
+        "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
+        "tri_trace_enable": ([i32], None),
+        "tri_trace_report": ([ctypes.c_char_p, sz], i64),
+    }
+    for name, (args, res) in sigs.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+
+
+def load(path: str | None = None):
+    """Load libtriinv.so (once).  Raises RuntimeError if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or SO_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"{p} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        _declare(lib)
+        _lib = lib
+        return lib
+
+
+# ---- C entry points, same names and argument order ------------------------------------
+
+def status_string(status: int) -> str:
+    return load().tri_status_string(int(status)).decode()
+
+
+def tri_version() -> str:
+    return load().tri_version().decode()
+
+
+def tri_inv(uplo, diag, n, ptr, ld, dtype, stream=0) -> int:
+    return load().tri_inv(uplo, diag, n, ptr, ld, dtype, stream or None)
+
+
+def tri_inv_workspace_size(n, dtype) -> int:
+    return int(load().tri_inv_workspace_size(n, dtype))
+
+
+def tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
+    return load().tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace or None, ws_bytes,
+                             stream or None)
+
+
+def tri_get_info(stream=0):
+    """Returns (status, first_bad_index)."""
+    idx = ctypes.c_int64(-1)
+    st = load().tri_get_info(stream or None, ctypes.byref(idx))
+    return st, idx.value
+
+
+def tri_trace_enable(on: bool):
+    load().tri_trace_enable(1 if on else 0)
+
+
+def tri_trace_report() -> dict:
+    import json
+    lib = load()
+    need = lib.tri_trace_report(None, 0)
+    if need < 0:
+        raise TriError(TRI_ERR_CUDA, "tri_trace_report")
+    buf = ctypes.create_string_buffer(int(need) + 1)
+    lib.tri_trace_report(buf, len(buf))
+    return json.loads(buf.value.decode())
+
+
+def check(status: int, what: str = ""):
+    if status != TRI_OK:
+        raise TriError(status, what)
+
+
+# ---- torch helpers ----------------------------------------------------------------
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dtype_code(t, mixed: bool) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        if mixed:
+            raise ValueError("mixed precision is defined for float32 storage only")
+        return TRI_F64
+    if t.dtype == torch.float32:
+        return TRI_F32_MIXED if mixed else TRI_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _rowmajor_square(t):
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError("expected a square matrix")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.stride(1) != 1:
+        raise ValueError("expected unit stride along the last dimension")
+
+
+def inv_(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=None):
+    """In place: the ``lower`` (or upper) triangle of the row-major CUDA tensor ``t``
+    becomes that of t^-1; the other triangle is not touched."""
+    _rowmajor_square(t)
+    n = t.shape[0]
+    # Row-major lower == column-major upper with lda = stride(0).
+    uplo = TRI_UPPER if lower else TRI_LOWER
+    st = tri_inv(uplo, TRI_UNIT if unit else TRI_NONUNIT, n, t.data_ptr(), max(1, t.stride(0)),
+                 _dtype_code(t, mixed), _stream_handle(stream))
+    check(st, "tri_inv")
+    return t
+
+
+def inv(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=None):
+    """Out of place: returns the triangular inverse as a clean tril/triu tensor (the
+    diagonal is 1 when ``unit``)."""
+    import torch
+    out = t.contiguous().clone()
+    inv_(out, lower=lower, unit=unit, mixed=mixed, stream=stream)
+    out = torch.tril(out) if lower else torch.triu(out)
+    if unit:
+        out.diagonal().fill_(1)
+    return out
