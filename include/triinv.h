@@ -100,6 +100,34 @@ TRI_API size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype);
 TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
                       tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * tri_inv_noalloc -- tri_inv for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is an integration entry point.
+ *
+ * Some callers cannot call cudaMalloc: an application whose own memory manager has
+ * already reserved the device's memory (an allocation made inside the library would
+ * fail or fragment that pool), or latency-critical code that must neither block in the
+ * CUDA allocator nor handle an allocation failure halfway through its work.  This entry
+ * point computes exactly what tri_inv computes for TRI_F32 and TRI_F64, but keeps its
+ * scratch in a fixed device array of TRI_NOALLOC_SCRATCH_BYTES that the library holds on
+ * every GPU that loads it, until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The caller still passes the matrix (same arguments and
+ * layout as tri_inv).
+ *   - Sizes whose scratch (tri_inv_workspace_size(n, dtype)) exceeds the array return
+ *     TRI_ERR_ARG before anything is queued: TRI_F32 up to n = 4096, TRI_F64 up to
+ *     n = 2048.  TRI_F32_MIXED returns TRI_ERR_UNSUPPORTED.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *     capture begins on that device.
+ *   - Every call on a device shares the one array, which keeps the previous call's
+ *     contents (no call reads scratch it has not written itself).  Calls whose GPU work
+ *     can overlap -- on different streams, or from host threads without ordering -- race
+ *     on the array and give wrong results: order them on one stream.
+ * --------------------------------------------------------------------------------- */
+#define TRI_NOALLOC_SCRATCH_BYTES (16u << 20)
+TRI_API tri_status tri_inv_noalloc(tri_uplo uplo, tri_diag diag, int64_t n, void *a,
+                                   int64_t lda, tri_dtype dtype, void *stream);
+
 /* Synchronises `stream`, then reports and clears the device-side status of the calling
  * thread's current device: TRI_ERR_SINGULAR with *first_bad_index set to the smallest
  * bad pivot index recorded since the last call, TRI_ERR_TIMEOUT if a bounded wait ran

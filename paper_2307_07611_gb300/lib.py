@@ -43,6 +43,7 @@ def _declare(lib):
         "tri_inv_workspace_size": ([i64, i32], sz),
         "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
+        "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "tri_trace_enable": ([i32], None),
         "tri_trace_report": ([ctypes.c_char_p, sz], i64),
     }
@@ -91,6 +92,16 @@ def tri_inv_workspace_size(n, dtype) -> int:
 def tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
     return load().tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace or None, ws_bytes,
                              stream or None)
+
+
+TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def tri_inv_noalloc(uplo, diag, n, ptr, ld, dtype, stream=0) -> int:
+    """tri_inv for callers that cannot allocate device memory: the scratch lives in a
+    fixed 16 MiB device array held by the library (FP32 up to n = 4096, FP64 up to
+    n = 2048).  Calls that overlap on the GPU share that array and race."""
+    return load().tri_inv_noalloc(uplo, diag, n, ptr, ld, dtype, stream or None)
 
 
 def tri_get_info(stream=0):
