@@ -128,6 +128,23 @@ TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, 
 TRI_API tri_status tri_inv_noalloc(tri_uplo uplo, tri_diag diag, int64_t n, void *a,
                                    int64_t lda, tri_dtype dtype, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * tri_tc_gemm_bf16 -- the tensor-core product kernel of the mixed path on plain operands,
+ * exposed for verification: C = sum_{t < nterms} A_t B_t, the dense "triangular times
+ * full" products of the split (Section 4.1, Eq. "ptfm") before any triangular masking.
+ *   A_t: m x k BF16, column-major, leading dimension lda (multiple of 8);
+ *   B_t: k x n BF16, column-major, leading dimension ldb (multiple of 8);
+ *   a_planes / b_planes: HOST arrays of nterms (1..3) device pointers, 16-byte aligned;
+ *   C: m x n FP32, column-major, ldc >= m, overwritten.
+ * Products are exact in FP32 (BF16 x BF16) and accumulated in FP32 in tensor memory.
+ * Errors: TRI_ERR_ARG for bad sizes, alignment or pointers; TRI_ERR_NOMEM if the tile list
+ * cannot be allocated (stream-ordered).
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_tc_gemm_bf16(int64_t m, int64_t n, int64_t k, int nterms,
+                                    const void *const *a_planes, int64_t lda,
+                                    const void *const *b_planes, int64_t ldb, float *c,
+                                    int64_t ldc, void *stream);
+
 /* Synchronises `stream`, then reports and clears the device-side status of the calling
  * thread's current device: TRI_ERR_SINGULAR with *first_bad_index set to the smallest
  * bad pivot index recorded since the last call, TRI_ERR_TIMEOUT if a bounded wait ran

@@ -70,6 +70,12 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     return TRI_OK;
 }
 
+}  // namespace
+
+tri_status device_ctx_public(cudaStream_t stream, Ctx *out) { return device_ctx(stream, out); }
+
+namespace {
+
 // ---- tracing -------------------------------------------------------------------------
 struct TraceRec {
     std::string kernel;
@@ -143,11 +149,15 @@ bool valid_enums(tri_uplo u, tri_diag d, tri_dtype t) {
 
 tri_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA; }
 
-tri_status run_plain(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
-                     int64_t lda, void *ws) {
+}  // namespace
+
+// Leaf inverses and the split levels with half-size h < hmax (hmax = n: the whole
+// recursion; hmax = 256: only the diagonal 256-blocks, as the mixed path needs).
+tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
+                            int64_t lda, void *ws, int64_t hmax) {
     cudaError_t e = launch_leaf(c, dt, trans, unit, n, a, lda, kLeafPlain);
     if (e != cudaSuccess) return TRI_ERR_CUDA;
-    for (int64_t h = kLeafPlain; h < n; h *= 2) {
+    for (int64_t h = kLeafPlain; h < n && h < hmax; h *= 2) {
         e = launch_trmm_level(c, dt, trans, unit, 0, n, a, lda, h, ws);
         if (e != cudaSuccess) return TRI_ERR_CUDA;
         e = launch_trmm_level(c, dt, trans, unit, 1, n, a, lda, h, ws);
@@ -156,7 +166,9 @@ tri_status run_plain(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t 
     return TRI_OK;
 }
 
-}  // namespace
+size_t mixed_ws_bytes(int64_t n);
+tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws);
+
 }  // namespace triinv
 
 using namespace triinv;
@@ -181,6 +193,7 @@ const char *tri_version(void) { return "0.1.0 sm_103a"; }
 size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype) {
     if (n <= 0) return 0;
     if (dtype == TRI_F64 || dtype == TRI_F32) return plain_ws_bytes(n, dtype);
+    if (dtype == TRI_F32_MIXED) return mixed_ws_bytes(n);
     return 0;
 }
 
@@ -189,14 +202,15 @@ tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t 
     if (!valid_enums(uplo, diag, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
     if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
-    if (dtype == TRI_F32_MIXED) return TRI_ERR_UNSUPPORTED;
     const size_t need = tri_inv_workspace_size(n, dtype);
     if (need > 0 && (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)))
         return TRI_ERR_NOMEM;
     Ctx c;
     tri_status st = device_ctx((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
-    return run_plain(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, workspace);
+    if (dtype == TRI_F32_MIXED)
+        return run_mixed(c, uplo == TRI_UPPER, diag == TRI_UNIT, n, (float *)a, lda, workspace);
+    return run_plain_levels(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, workspace, n);
 }
 
 tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,

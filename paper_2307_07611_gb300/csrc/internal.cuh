@@ -27,6 +27,9 @@ __host__ __device__ __forceinline__ int64_t vidx(int64_t i, int64_t j, int64_t l
     return TRANS ? (j + i * ld) : (i + j * ld);
 }
 
+// Launch context of the calling thread's current device (api.cu).
+tri_status device_ctx_public(cudaStream_t stream, Ctx *out);
+
 // ---- tracing (api.cu) -------------------------------------------------------------
 // While tracing is on, TraceScope records a CUDA event pair around the launches made in
 // its lifetime on `stream`, and books the launch's algorithmic flops and bytes.

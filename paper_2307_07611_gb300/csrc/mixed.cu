@@ -1,0 +1,239 @@
+// mixed.cu -- the TRI_F32_MIXED path: recursive split with split-BF16 tensor-core
+// products, followed by one Newton-Schulz step.
+//
+// 1. T (FP32) -> BF16 planes T_hi, T_mid, T_lo                       (split.cu)
+// 2. every 256 x 256 diagonal block is inverted in FP32: CRIT leaves of 64 and the two
+//    lowest split levels on CUDA cores                                (leaf.cu, trmm_simt.cu)
+// 3. those diagonal blocks of X -> BF16 planes X_hi, X_mid, X_lo     (split.cu)
+// 4. split levels h = 256, 512, ...: for every pair (block inverse of the proof of the
+//    main Theorem, Section 3; Algorithm COMBRIT with two blocks, Section 4.1)
+//        W   = B X_A       3 terms  hi*hi + hi*mid + mid*hi   -> W_hi, W_mid
+//        X21 = -X_C W      3 terms                              -> X (FP32) and its planes
+// 5. Newton-Schulz step X <- X (2I - T X) = X + X R:
+//        R = I - T X       6 terms (hh, hm, mh, hl, mm, lh): ~2^-24 relative accuracy;
+//                          R is a difference of nearly equal terms, of the order of the
+//                          3-term error (~1e-5), and is stored as hi/mid planes
+//        X += X R          3 terms: a 1-term BF16 product would leave an error of
+//                          2^-8 |X R| ~ 4e-8 normwise, above plain FP32's residual
+// The tile lists of every product depend on n only and are built once per (device, n)
+// and kept in device memory.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "tc_gemm.cuh"
+
+namespace triinv {
+
+cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
+                                const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
+                                __nv_bfloat16 *p2, int64_t ldp);
+
+namespace {
+
+constexpr int64_t kDiag = 256;      // diagonal blocks inverted on CUDA cores
+constexpr int64_t kLeaf = 64;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+int64_t cdiv(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+struct Layout {
+    int64_t ldp;
+    size_t off_t, off_x, off_r, off_w, off_s, total;
+    int64_t wmax;    // elements of one W plane (largest level)
+};
+
+Layout layout(int64_t n) {
+    Layout L{};
+    L.ldp = round_up(std::max<int64_t>(n, 1), 64);
+    const size_t plane = (size_t)L.ldp * (size_t)n * 2;
+    L.wmax = 0;
+    for (int64_t h = kDiag; h < n; h *= 2) L.wmax = std::max(L.wmax, level_pairs(n, h) * h * h);
+    size_t sbytes = 0;
+    for (int64_t h = kLeaf; h < std::min(n, kDiag); h *= 2)
+        sbytes = std::max(sbytes, (size_t)(level_pairs(n, h) * h * h) * 4);
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    L.off_t = 0;
+    L.off_x = L.off_t + 3 * al(plane);
+    L.off_r = L.off_x + 3 * al(plane);
+    L.off_w = L.off_r + 2 * al(plane);
+    L.off_s = L.off_w + 2 * al((size_t)L.wmax * 2);
+    L.total = L.off_s + al(sbytes);
+    return L;
+}
+
+struct Launch {
+    int first, count;
+    double flops;
+};
+
+struct Plan {
+    tc::Tile *d_tiles = nullptr;
+    std::vector<Launch> w, x21;   // per tc level
+    Launch res{}, upd{};
+};
+
+std::mutex g_plan_mu;
+std::map<std::pair<int, int64_t>, Plan> g_plans;
+
+void sort_longest_first(std::vector<tc::Tile> &v, size_t from) {
+    std::stable_sort(v.begin() + from, v.end(), [](const tc::Tile &a, const tc::Tile &b) {
+        return (a.kb1 - a.kb0) > (b.kb1 - b.kb0);
+    });
+}
+
+tri_status build_plan(int dev, int64_t n, Plan **out) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto key = std::make_pair(dev, n);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        *out = &it->second;
+        return TRI_OK;
+    }
+    Plan p;
+    std::vector<tc::Tile> v;
+    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops) {
+        sort_longest_first(v, from);
+        Launch l{(int)from, (int)(v.size() - from), flops};
+        if (vec) vec->push_back(l);
+        else *one = l;
+    };
+    for (int64_t h = kDiag; h < n; h *= 2) {
+        const int64_t P = level_pairs(n, h);
+        // W = B X_A  (W is h x P*h, pair q in columns [q*h, q*h + h))
+        size_t from = v.size();
+        double fl = 0.0;
+        for (int64_t q = 0; q < P; ++q) {
+            const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
+            fl += 3.0 * (double)hc * h * (h + 1);
+            for (int64_t tn = 0; tn < h / tc::BN; ++tn)
+                for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm)
+                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * tc::BN),
+                                         (int)(tn * tc::BN / tc::BK), (int)(h / tc::BK),
+                                         (int)(tm * tc::BM), (int)(q * h + tn * tc::BN)});
+        }
+        add(&p.w, nullptr, from, fl);
+        // X21 = -X_C W
+        from = v.size();
+        fl = 0.0;
+        for (int64_t q = 0; q < P; ++q) {
+            const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
+            fl += 3.0 * (double)h * hc * (hc + 1);
+            for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
+                const int64_t kend = std::min((tm + 1) * tc::BM, hc);
+                for (int64_t tn = 0; tn < h / tc::BN; ++tn)
+                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)c0, 0, (int)(q * h + tn * tc::BN), 0,
+                                         (int)cdiv(kend, tc::BK), (int)(c0 + tm * tc::BM),
+                                         (int)(a0 + tn * tc::BN)});
+            }
+        }
+        add(&p.x21, nullptr, from, fl);
+    }
+    // Newton-Schulz: lower x lower products over the whole matrix.
+    const double lower_prod = (double)n * (n + 1) * (n + 2) / 3.0;   // 2 * sum_{i>=j} (i-j+1)
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t from = v.size();
+        for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
+            const int64_t kend = std::min((tm + 1) * tc::BM, n);
+            for (int64_t tn = 0; tn * tc::BN < kend; ++tn)
+                v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
+                                     (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
+        }
+        add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 3.0) * lower_prod);
+    }
+    if (!v.empty()) {
+        if (cudaMalloc(&p.d_tiles, v.size() * sizeof(tc::Tile)) != cudaSuccess) {
+            cudaGetLastError();
+            return TRI_ERR_NOMEM;
+        }
+        if (cudaMemcpy(p.d_tiles, v.data(), v.size() * sizeof(tc::Tile), cudaMemcpyHostToDevice) != cudaSuccess)
+            return TRI_ERR_CUDA;
+    }
+    auto res = g_plans.emplace(key, p);
+    *out = &res.first->second;
+    return TRI_OK;
+}
+
+}  // namespace
+
+size_t mixed_ws_bytes(int64_t n) {
+    if (n <= kDiag) {
+        size_t best = 0;
+        for (int64_t h = kLeaf; h < n; h *= 2) best = std::max(best, (size_t)(level_pairs(n, h) * h * h) * 4);
+        return best;
+    }
+    return layout(n).total;
+}
+
+tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
+                            int64_t lda, void *ws, int64_t hmax);
+
+tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws) {
+    if (n <= kDiag) return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
+    const Layout L = layout(n);
+    uint8_t *base = (uint8_t *)ws;
+    const size_t plane = ((size_t)L.ldp * (size_t)n * 2 + 255) / 256 * 256;
+    __nv_bfloat16 *T[3], *X[3], *R[2], *W[2];
+    for (int i = 0; i < 3; ++i) {
+        T[i] = (__nv_bfloat16 *)(base + L.off_t + i * plane);
+        X[i] = (__nv_bfloat16 *)(base + L.off_x + i * plane);
+    }
+    R[0] = (__nv_bfloat16 *)(base + L.off_r);
+    R[1] = (__nv_bfloat16 *)(base + L.off_r + plane);
+    const size_t wplane = ((size_t)L.wmax * 2 + 255) / 256 * 256;
+    W[0] = (__nv_bfloat16 *)(base + L.off_w);
+    W[1] = (__nv_bfloat16 *)(base + L.off_w + wplane);
+    void *scratch = base + L.off_s;
+
+    Plan *plan = nullptr;
+    tri_status st = build_plan(c.device, n, &plan);
+    if (st != TRI_OK) return st;
+
+    // 1. T planes
+    if (launch_split_planes(c, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp) != cudaSuccess)
+        return TRI_ERR_CUDA;
+    // 2. FP32 diagonal blocks of 256
+    st = run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, scratch, kDiag);
+    if (st != TRI_OK) return st;
+    // 3. their planes
+    if (launch_split_planes(c, trans, unit, true, n, a, lda, X[0], X[1], X[2], L.ldp) != cudaSuccess)
+        return TRI_ERR_CUDA;
+
+    auto pl = [&](const __nv_bfloat16 *p, int64_t rows, int64_t cols, int64_t ld) {
+        return tc::Plane{p, rows, cols, ld};
+    };
+    const tc::Plane tp[3] = {pl(T[0], n, n, L.ldp), pl(T[1], n, n, L.ldp), pl(T[2], n, n, L.ldp)};
+    const tc::Plane xp[3] = {pl(X[0], n, n, L.ldp), pl(X[1], n, n, L.ldp), pl(X[2], n, n, L.ldp)};
+    const tc::Terms three{3, {0, 0, 1}, {0, 1, 0}};
+    // 4. tensor-core levels
+    int lvl = 0;
+    for (int64_t h = kDiag; h < n; h *= 2, ++lvl) {
+        const int64_t P = level_pairs(n, h);
+        const tc::Plane wp[2] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h)};
+        tc::Epi ew{nullptr, 0, W[0], W[1], nullptr, h, h, P * h};
+        const Launch &lw = plan->w[lvl];
+        if (tc::launch_tc(c, tc::MODE_W, trans, unit, tp, 3, xp, 3, three, plan->d_tiles + lw.first,
+                          lw.count, ew, lw.flops, "tc_gemm:w") != cudaSuccess)
+            return TRI_ERR_CUDA;
+        tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
+        const Launch &lx = plan->x21[lvl];
+        if (tc::launch_tc(c, tc::MODE_X21, trans, unit, xp, 3, wp, 2, three, plan->d_tiles + lx.first,
+                          lx.count, ex, lx.flops, "tc_gemm:x21") != cudaSuccess)
+            return TRI_ERR_CUDA;
+    }
+    // 5. Newton-Schulz: R = I - T X, then X += X R
+    const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
+    tc::Epi er{nullptr, 0, R[0], R[1], nullptr, L.ldp, n, n};
+    if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
+                      plan->res.count, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
+        return TRI_ERR_CUDA;
+    const tc::Plane rp[2] = {pl(R[0], n, n, L.ldp), pl(R[1], n, n, L.ldp)};
+    tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
+    if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 2, rp, 2, three, plan->d_tiles + plan->upd.first,
+                      plan->upd.count, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
+        return TRI_ERR_CUDA;
+    return TRI_OK;
+}
+
+}  // namespace triinv

@@ -1,0 +1,588 @@
+// tc_gemm.cu -- K3: split-BF16 products on the 5th-generation tensor cores (tcgen05).
+//
+// Computes, per output tile, acc = sum_t A_t * B_t with BF16 operands and an FP32
+// accumulator in tensor memory, where the A_t / B_t are BF16 "planes" of FP32 matrices
+// (x = hi + mid + lo, each piece rounded to BF16).  It serves every dense product of the
+// mixed-precision path:
+//   level products of the split (block inverse, proof of the main Theorem, Section 3):
+//       W = B X_A (3 terms)  and  X21 = -X_C W (3 terms);
+//   the Newton-Schulz step X <- X + X (I - T X): R = I - T X (6 terms), X += X R (3 terms).
+//
+// Structure (one CTA per SM, persistent over a host-built tile list, longest first):
+//   warp 0      TMA producer: per (k-block, term) one pipeline slot = A tile 128x64
+//               (two 64x64 boxes, MN-major) + B tile 256x64 (K-major), 128-byte swizzle.
+//   warp 1      allocates 512 TMEM columns (two 128x256 FP32 accumulators), one lane
+//               issues tcgen05.mma (M=128, N=256, K=16) and commits slots / accumulators.
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator (two warps per 32-lane quarter,
+//               128 columns each), split / update / store, then release the accumulator.
+// The epilogue of tile i overlaps the main loop of tile i+1 (double-buffered TMEM).
+// Every mbarrier wait is bounded (globaltimer); on timeout the kernel records the status,
+// drains its in-flight copies and products, frees TMEM and returns.
+//
+// Operand layouts in shared memory (canonical tcgen05 layouts, 128-byte swizzle):
+//   A (MN-major): atom = 64 M-elements (128 B) x 8 K-rows; M atoms 8192 B apart (LBO),
+//                 K atoms 1024 B apart (SBO).  One MMA (K = 16) spans two K atoms.
+//   B (K-major):  atom = 8 N-rows x 64 K-elements (128 B); N atoms 1024 B apart (SBO);
+//                 the k-offset inside the 128-byte row advances the start address by 32 B.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "tc_gemm.cuh"
+
+namespace triinv {
+namespace tc {
+namespace {
+
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+constexpr int B_BYTES = BN * BK * 2;          // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 512;
+constexpr int EPI_WARPS = 8;                  // two per TMEM lane quarter
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;   // 4 s per wait
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
+// 10-12 = 1), A MN-major (bit 15), B K-major (bit 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) |
+                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait.  Returns false if the CTA is aborting or the deadline passed (then it
+// raises the abort flag and the device timeout word).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          int *gtimeout) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitLimitNs) {
+                *abort_flag = 1;
+                atomicExch(gtimeout, 1);
+                return false;
+            }
+        }
+    }
+}
+
+// Wait used while draining after an abort: deadline only.
+__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer() - t0 > kWaitLimitNs) return;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap *map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4
+// (32-45), version 1 (46-47), base offset 0, swizzle mode 2 = 128-byte (61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 8 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Maps {
+    CUtensorMap a[3];
+    CUtensorMap b[3];
+};
+
+// Stores NC accumulator columns gn0..gn0+NC-1 of row gm (one thread = one row).
+// Column-major targets advance by one leading dimension per column, so the 32 threads of
+// a warp (32 consecutive rows) write contiguous bytes for every column.
+template <int MODE, bool TRANS, bool UNIT, int NC>
+__device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t gn0,
+                                              const uint32_t (&r)[NC]) {
+    if (gm >= ep.mlim) return;
+    const int64_t left = ep.nlim - gn0;
+    if (MODE == MODE_W || MODE == MODE_X21 || MODE == MODE_RES) {
+        int64_t off = gm + gn0 * ep.ldo;
+        int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+        const int64_t xstep = TRANS ? 1 : ep.ldx;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (j < left) {
+                const float acc = __uint_as_float(r[j]);
+                float v = acc;
+                if (MODE == MODE_X21) {
+                    v = -acc;
+                    ep.x[xo] = v;
+                } else if (MODE == MODE_RES) {
+                    const int64_t gn = gn0 + j;
+                    v = gm >= gn ? ((gm == gn ? 1.f : 0.f) - acc) : 0.f;
+                }
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                const float r1 = v - __bfloat162float(h);
+                const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                ep.o0[off] = h;
+                ep.o1[off] = m;
+                if (MODE == MODE_X21) ep.o2[off] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            }
+            off += ep.ldo;
+            xo += xstep;
+        }
+    } else if (MODE == MODE_UPD) {
+        int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+        const int64_t xstep = TRANS ? 1 : ep.ldx;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int64_t gn = gn0 + j;
+            if (j < left && (gm > gn || (!UNIT && gm == gn))) ep.x[xo] += __uint_as_float(r[j]);
+            xo += xstep;
+        }
+    } else {
+        int64_t xo = gm + gn0 * ep.ldx;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (j < left) ep.x[xo] = __uint_as_float(r[j]);
+            xo += ep.ldx;
+        }
+    }
+}
+
+// Number of k-blocks accumulated in tensor memory before the epilogue adds them into
+// FP32 registers (MODE_RES only).  The tensor-core accumulator truncates each add, so a
+// long accumulation drifts towards zero by up to one unit in the last place per MMA; a
+// 256-wide chunk keeps that drift at the size of IEEE FP32 rounding of the whole sum.
+constexpr int kPromoteBlocks = 4;
+
+template <int MODE, bool TRANS, bool UNIT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
+               const Tile *__restrict__ tiles, const int ntiles, const Epi ep, int *gtimeout) {
+    constexpr bool PROMOTE = (MODE == MODE_RES);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+    // k-blocks per accumulation chunk: one chunk per tile unless promoting.
+    auto chunk_blocks = [&](const Tile &tl) { return PROMOTE ? kPromoteBlocks : (tl.kb1 - tl.kb0); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), EPI_WARPS);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        for (int i = 0; i < 3; ++i) {
+            prefetch_map(&maps.a[i]);
+            prefetch_map(&maps.b[i]);
+        }
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            // Order: chunk, then term from the smallest pieces to hi*hi, then k-block.
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const Tile tl = tiles[t];
+                const int cb = chunk_blocks(tl);
+                for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb) {
+                    const int c1 = min(c0 + cb, tl.kb1);
+                    for (int j = terms.n - 1; j >= 0 && ok; --j) {
+                        const CUtensorMap *am = &maps.a[terms.a[j]];
+                        const CUtensorMap *bm = &maps.b[terms.b[j]];
+                        for (int kb = c0; kb < c1; ++kb) {
+                            const int s = it % STAGES;
+                            const uint32_t ph = (it / STAGES) & 1u;
+                            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, gtimeout)) {
+                                ok = false;
+                                break;
+                            }
+                            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                            const uint32_t sb = sa + A_BYTES;
+                            mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+                            const int k = kb * BK;
+                            tma_load_2d(sa, am, tl.am, tl.ak + k, full_bar(s));
+                            tma_load_2d(sa + A_BYTES / 2, am, tl.am + 64, tl.ak + k, full_bar(s));
+                            tma_load_2d(sb, bm, tl.bk + k, tl.bn, full_bar(s));
+                            ++it;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the copies already issued land before the CTA exits.
+                const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0u;
+                for (uint32_t j = first; j < it; ++j) mbar_wait_drain(full_bar(j % STAGES), (j / STAGES) & 1u);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            uint32_t it = 0, lc = 0;
+            bool ok = true, issued = false;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const Tile tl = tiles[t];
+                const int cb = chunk_blocks(tl);
+                for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb, ++lc) {
+                    const int c1 = min(c0 + cb, tl.kb1);
+                    const uint32_t a = lc & 1u, use = lc >> 1;
+                    if (!mbar_wait(tempty_bar(a), (use & 1u) ^ 1u, abort_flag, gtimeout)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + a * (uint32_t)BN;
+                    uint32_t accumulate = 0;
+                    for (int j = terms.n - 1; j >= 0 && ok; --j) {
+                        for (int kb = c0; kb < c1; ++kb) {
+                            const int s = it % STAGES;
+                            const uint32_t ph = (it / STAGES) & 1u;
+                            if (!mbar_wait(full_bar(s), ph, abort_flag, gtimeout)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const uint64_t da = smem_desc(sa + kk * 2048, 8192, 1024);
+                                const uint64_t db = smem_desc(sb + kk * 32, 16, 1024);
+                                tc_mma(d, da, db, kIdesc, accumulate);
+                                accumulate = 1;
+                            }
+                            issued = true;
+                            tc_commit(empty_bar(s));
+                            ++it;
+                        }
+                    }
+                    if (ok) tc_commit(tfull_bar(a));
+                }
+            }
+            if (!ok && issued) {
+                // Wait until every product issued so far has completed.
+                tc_commit(drain_bar);
+                mbar_wait_drain(drain_bar, 0);
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        // Warp w reads TMEM lane quarter (w % 4); warps 2-5 take columns 0-127 and warps
+        // 6-9 columns 128-255 of the accumulator.
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row = quarter * 32 + lane;
+        uint32_t lc = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const Tile tl = tiles[t];
+            const int cb = chunk_blocks(tl);
+            const int64_t gm = (int64_t)tl.om + row;
+            float sum[PROMOTE ? BN / 2 : 1];
+            if (PROMOTE) {
+#pragma unroll
+                for (int i = 0; i < BN / 2; ++i) sum[i] = 0.f;
+            }
+            for (int c0 = tl.kb0; c0 < tl.kb1; c0 += cb, ++lc) {
+                const uint32_t a = lc & 1u, use = lc >> 1;
+                if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + a * (uint32_t)BN + (uint32_t)(half * (BN / 2)) +
+                                       ((uint32_t)(quarter * 32) << 16);
+                if (PROMOTE) {
+#pragma unroll
+                    for (int q = 0; q < BN / 32; ++q) {
+                        uint32_t r[16];
+                        tmem_ld16(taddr + q * 16, r);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) sum[q * 16 + i] += __uint_as_float(r[i]);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int q = 0; q < BN / 16; ++q) {
+                        uint32_t r[8];
+                        tmem_ld8(taddr + q * 8, r);
+                        epilogue_cols<MODE, TRANS, UNIT, 8>(ep, gm, (int64_t)tl.on + half * (BN / 2) + q * 8, r);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty_bar(a));
+            }
+            if (PROMOTE && ok) {
+#pragma unroll
+                for (int q = 0; q < BN / 32; ++q) {
+                    uint32_t r[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(sum[q * 16 + i]);
+                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, gm, (int64_t)tl.on + half * (BN / 2) + q * 16, r);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---- host side ------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool get_encode() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode != nullptr;
+}
+
+// 2-D map over a column-major BF16 plane: inner dimension = rows, 128-byte swizzle,
+// box = box_rows x box_cols, zero fill outside [0, rows) x [0, cols).
+bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols) {
+    if (!get_encode()) return false;
+    if (((uintptr_t)p.p & 15) || (p.ld * 2) % 16 || p.rows <= 0 || p.cols <= 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)p.rows, (cuuint64_t)p.cols};
+    cuuint64_t strides[1] = {(cuuint64_t)(p.ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)p.p, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE, bool TRANS, bool UNIT>
+cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Tile *d_tiles,
+                     int ntiles, const Epi &epi) {
+    auto kern = tc_gemm_kernel<MODE, TRANS, UNIT>;
+    static bool attr_set[64] = {};
+    if (!attr_set[c.device]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set[c.device] = true;
+    }
+    const int grid = ntiles < c.sm_count ? ntiles : c.sm_count;
+    kern<<<grid, NTHREADS, SMEM_BYTES, c.stream>>>(maps, terms, d_tiles, ntiles, epi, c.timeout);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes, int na,
+                      const Plane *bplanes, int nb, const Terms &terms, const Tile *d_tiles,
+                      int ntiles, const Epi &epi, double flops, const char *trace_name) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
+    Maps maps;
+    memset(&maps, 0, sizeof(maps));
+    for (int i = 0; i < 3; ++i) {
+        const Plane &pa = aplanes[i < na ? i : 0];
+        const Plane &pb = bplanes[i < nb ? i : 0];
+        if (!encode_plane(&maps.a[i], pa, 64, 64)) return cudaErrorInvalidValue;
+        if (!encode_plane(&maps.b[i], pb, 64, BN)) return cudaErrorInvalidValue;
+    }
+    TraceScope ts(c.stream, trace_name, flops, 0.0);
+#define TRI_TC_CASE(M)                                                                   \
+    case M:                                                                              \
+        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, d_tiles, ntiles, epi)   \
+                               : launch_t<M, true, false>(c, maps, terms, d_tiles, ntiles, epi); \
+        return unit ? launch_t<M, false, true>(c, maps, terms, d_tiles, ntiles, epi)             \
+                    : launch_t<M, false, false>(c, maps, terms, d_tiles, ntiles, epi);
+    switch (mode) {
+        TRI_TC_CASE(MODE_W)
+        TRI_TC_CASE(MODE_X21)
+        TRI_TC_CASE(MODE_RES)
+        TRI_TC_CASE(MODE_UPD)
+        case MODE_F32:
+            return launch_t<MODE_F32, false, false>(c, maps, terms, d_tiles, ntiles, epi);
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef TRI_TC_CASE
+}
+
+}  // namespace tc
+}  // namespace triinv
+
+// Verification entry point: the product kernel on plain column-major BF16 operands.
+extern "C" tri_status tri_tc_gemm_bf16(int64_t m, int64_t n, int64_t k, int nterms,
+                                       const void *const *a_planes, int64_t lda,
+                                       const void *const *b_planes, int64_t ldb, float *c,
+                                       int64_t ldc, void *stream) {
+    using namespace triinv;
+    if (m < 0 || n < 0 || k < 0 || nterms < 1 || nterms > 3 || !a_planes || !b_planes) return TRI_ERR_ARG;
+    if (m == 0 || n == 0) return TRI_OK;
+    if (k == 0 || !c || ldc < m || lda < m || ldb < k || (lda % 8) || (ldb % 8)) return TRI_ERR_ARG;
+    if (m > (1ll << 30) || n > (1ll << 30) || k > (1ll << 30)) return TRI_ERR_ARG;
+    tc::Plane ap[3], bp[3];
+    for (int i = 0; i < nterms; ++i) {
+        if (!a_planes[i] || !b_planes[i] || ((uintptr_t)a_planes[i] & 15) || ((uintptr_t)b_planes[i] & 15))
+            return TRI_ERR_ARG;
+        ap[i] = tc::Plane{(const __nv_bfloat16 *)a_planes[i], m, k, lda};
+        bp[i] = tc::Plane{(const __nv_bfloat16 *)b_planes[i], k, n, ldb};
+    }
+    Ctx ctx;
+    tri_status st = device_ctx_public((cudaStream_t)stream, &ctx);
+    if (st != TRI_OK) return st;
+    std::vector<tc::Tile> v;
+    const int64_t kb = (k + tc::BK - 1) / tc::BK;
+    for (int64_t tm = 0; tm * tc::BM < m; ++tm)
+        for (int64_t tn = 0; tn * tc::BN < n; ++tn)
+            v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), 0, (int)kb, (int)(tm * tc::BM),
+                                 (int)(tn * tc::BN)});
+    tc::Tile *d = nullptr;
+    const size_t bytes = v.size() * sizeof(tc::Tile);
+    if (cudaMallocAsync((void **)&d, bytes, ctx.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    if (cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, ctx.stream) != cudaSuccess) return TRI_ERR_CUDA;
+    tc::Terms terms{nterms, {0, 1, 2}, {0, 1, 2}};
+    tc::Epi ep{c, ldc, nullptr, nullptr, nullptr, 0, m, n};
+    cudaError_t e = tc::launch_tc(ctx, tc::MODE_F32, false, false, ap, nterms, bp, nterms, terms, d,
+                                  (int)v.size(), ep, 2.0 * m * n * k * nterms, "tc_gemm:f32");
+    cudaFreeAsync(d, ctx.stream);
+    return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}

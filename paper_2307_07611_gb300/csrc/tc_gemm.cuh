@@ -1,0 +1,61 @@
+// tc_gemm.cuh -- interface of the tcgen05 split-BF16 product kernel (tc_gemm.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace triinv {
+namespace tc {
+
+constexpr int BM = 128;   // rows of an output tile (UMMA M)
+constexpr int BN = 256;   // columns of an output tile (UMMA N)
+constexpr int BK = 64;    // k-block staged per pipeline slot (one 128-byte swizzle row)
+
+// One output tile: operand A rows [am, am+128) and columns ak + [kb0*64, kb1*64);
+// operand B rows bk + [kb0*64, kb1*64) and columns [bn, bn+256); output origin (om, on).
+struct Tile {
+    int am, ak, bk, bn, kb0, kb1, om, on;
+};
+
+// Products summed into one FP32 accumulator: sum_t A_{a[t]} * B_{b[t]}.
+struct Terms {
+    int n;
+    int a[6];
+    int b[6];
+};
+
+// Epilogue targets (see the modes in tc_gemm.cu).
+struct Epi {
+    float *x;          // FP32 matrix (lower view through TRANS), leading dimension ldx
+    int64_t ldx;
+    __nv_bfloat16 *o0, *o1, *o2;   // BF16 output planes, column-major, leading dim ldo
+    int64_t ldo;
+    int64_t mlim, nlim;            // output rows / columns that exist
+};
+
+enum Mode {
+    MODE_W = 0,      // o0/o1 <- hi/lo BF16 split of acc                    (W = B X_A)
+    MODE_X21 = 1,    // x <- -acc; o0/o1/o2 <- hi/mid/lo split of -acc      (X21 = -X_C W)
+    MODE_RES = 2,    // o0/o1 <- hi/lo split of I - acc (lower), 0 above    (R = I - T X)
+    MODE_UPD = 3,    // x += acc on the lower triangle                       (X += X R)
+    MODE_F32 = 4,    // x <- acc (plain column-major store, no view)        (verification)
+};
+
+// A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld
+// (elements, multiple of 8), device pointer 16-byte aligned.
+struct Plane {
+    const __nv_bfloat16 *p;
+    int64_t rows, cols, ld;
+};
+
+// Encodes the tensor maps, then launches the persistent kernel over `ntiles` tiles read
+// from device memory.  amaps/bmaps: up to 3 planes each, indexed by `terms`.
+cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
+                      int na, const Plane *bplanes, int nb, const Terms &terms,
+                      const Tile *d_tiles, int ntiles, const Epi &epi, double flops,
+                      const char *trace_name);
+
+}  // namespace tc
+}  // namespace triinv

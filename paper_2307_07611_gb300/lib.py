@@ -23,6 +23,7 @@ TRI_OK, TRI_ERR_ARG, TRI_ERR_SINGULAR, TRI_ERR_NOMEM, TRI_ERR_CUDA, TRI_ERR_TIME
 TRI_LOWER, TRI_UPPER = 0, 1
 TRI_NONUNIT, TRI_UNIT = 0, 1
 TRI_F64, TRI_F32, TRI_F32_MIXED = 0, 1, 2
+MIXED_AVAILABLE = True
 
 _lock = threading.Lock()
 _lib = None
@@ -44,6 +45,8 @@ def _declare(lib):
         "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
+        "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
+                              vp, i64, vp], i32),
         "tri_trace_enable": ([i32], None),
         "tri_trace_report": ([ctypes.c_char_p, sz], i64),
     }
@@ -102,6 +105,15 @@ def tri_inv_noalloc(uplo, diag, n, ptr, ld, dtype, stream=0) -> int:
     fixed 16 MiB device array held by the library (FP32 up to n = 4096, FP64 up to
     n = 2048).  Calls that overlap on the GPU share that array and race."""
     return load().tri_inv_noalloc(uplo, diag, n, ptr, ld, dtype, stream or None)
+
+
+def tri_tc_gemm_bf16(m, n, k, a_ptrs, lda, b_ptrs, ldb, c, ldc, stream=0) -> int:
+    """C = sum_t A_t B_t on the tensor cores (BF16 planes in, FP32 out); a_ptrs / b_ptrs
+    are sequences of device pointers."""
+    nt = len(a_ptrs)
+    arr_a = (ctypes.c_void_p * nt)(*a_ptrs)
+    arr_b = (ctypes.c_void_p * nt)(*b_ptrs)
+    return load().tri_tc_gemm_bf16(m, n, k, nt, arr_a, lda, arr_b, ldb, c, ldc, stream or None)
 
 
 def tri_get_info(stream=0):
