@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true",
+                   help="skip the plain FP32 comparison run (for profiler launch lists)")
     p.add_argument("--no-quality", action="store_true",
                    help="skip the residual / oracle check (for profiler launch lists)")
     p.add_argument("--cpu-sample-stride", type=int, default=1)
@@ -276,7 +278,7 @@ def main():
     if not args.no_quality:
         resid, err, st_info = quality(code)
     extra = {}
-    if mode == "mixed":
+    if mode == "mixed" and not args.no_plain:
         p_total, _, _ = timed(lib.TRI_F32, max(3, args.steps // 2), 2)
         p_resid = p_err = None
         if not args.no_quality:

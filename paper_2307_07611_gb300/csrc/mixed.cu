@@ -64,12 +64,13 @@ Layout layout(int64_t n) {
 }
 
 struct Launch {
-    int first, count;
+    int first, ctas, off_first;   // tiles from `first`, CTA offsets from `off_first`
     double flops;
 };
 
 struct Plan {
     tc::Tile *d_tiles = nullptr;
+    int *d_off = nullptr;
     std::vector<Launch> w, x21;   // per tc level
     Launch res{}, upd{};
 };
@@ -77,13 +78,7 @@ struct Plan {
 std::mutex g_plan_mu;
 std::map<std::pair<int, int64_t>, Plan> g_plans;
 
-void sort_longest_first(std::vector<tc::Tile> &v, size_t from) {
-    std::stable_sort(v.begin() + from, v.end(), [](const tc::Tile &a, const tc::Tile &b) {
-        return (a.kb1 - a.kb0) > (b.kb1 - b.kb0);
-    });
-}
-
-tri_status build_plan(int dev, int64_t n, Plan **out) {
+tri_status build_plan(int dev, int sm_count, int64_t n, Plan **out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto key = std::make_pair(dev, n);
     auto it = g_plans.find(key);
@@ -93,9 +88,14 @@ tri_status build_plan(int dev, int64_t n, Plan **out) {
     }
     Plan p;
     std::vector<tc::Tile> v;
-    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops) {
-        sort_longest_first(v, from);
-        Launch l{(int)from, (int)(v.size() - from), flops};
+    std::vector<int> offs;
+    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms) {
+        std::vector<tc::Tile> part(v.begin() + from, v.end());
+        std::vector<int> o;
+        const int ctas = part.empty() ? 0 : tc::schedule_lpt(part, terms, sm_count, o);
+        std::copy(part.begin(), part.end(), v.begin() + from);
+        Launch l{(int)from, ctas, (int)offs.size(), flops};
+        for (int x : o) offs.push_back(x);
         if (vec) vec->push_back(l);
         else *one = l;
     };
@@ -113,7 +113,7 @@ tri_status build_plan(int dev, int64_t n, Plan **out) {
                                          (int)(tn * tc::BN / tc::BK), (int)(h / tc::BK),
                                          (int)(tm * tc::BM), (int)(q * h + tn * tc::BN)});
         }
-        add(&p.w, nullptr, from, fl);
+        add(&p.w, nullptr, from, fl, 3);
         // X21 = -X_C W
         from = v.size();
         fl = 0.0;
@@ -128,7 +128,7 @@ tri_status build_plan(int dev, int64_t n, Plan **out) {
                                          (int)(a0 + tn * tc::BN)});
             }
         }
-        add(&p.x21, nullptr, from, fl);
+        add(&p.x21, nullptr, from, fl, 3);
     }
     // Newton-Schulz: lower x lower products over the whole matrix.
     const double lower_prod = (double)n * (n + 1) * (n + 2) / 3.0;   // 2 * sum_{i>=j} (i-j+1)
@@ -140,15 +140,21 @@ tri_status build_plan(int dev, int64_t n, Plan **out) {
                 v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
                                      (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
         }
-        add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 3.0) * lower_prod);
+        add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 3.0) * lower_prod,
+            pass == 0 ? 6 : 3);
     }
     if (!v.empty()) {
-        if (cudaMalloc(&p.d_tiles, v.size() * sizeof(tc::Tile)) != cudaSuccess) {
+        const size_t tb = v.size() * sizeof(tc::Tile), ob = offs.size() * sizeof(int);
+        uint8_t *d = nullptr;
+        if (cudaMalloc(&d, tb + ob) != cudaSuccess) {
             cudaGetLastError();
             return TRI_ERR_NOMEM;
         }
-        if (cudaMemcpy(p.d_tiles, v.data(), v.size() * sizeof(tc::Tile), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpy(d, v.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d + tb, offs.data(), ob, cudaMemcpyHostToDevice) != cudaSuccess)
             return TRI_ERR_CUDA;
+        p.d_tiles = (tc::Tile *)d;
+        p.d_off = (int *)(d + tb);
     }
     auto res = g_plans.emplace(key, p);
     *out = &res.first->second;
@@ -187,7 +193,7 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     void *scratch = base + L.off_s;
 
     Plan *plan = nullptr;
-    tri_status st = build_plan(c.device, n, &plan);
+    tri_status st = build_plan(c.device, c.sm_count, n, &plan);
     if (st != TRI_OK) return st;
 
     // 1. T planes
@@ -214,24 +220,24 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         tc::Epi ew{nullptr, 0, W[0], W[1], nullptr, h, h, P * h};
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, tc::MODE_W, trans, unit, tp, 3, xp, 3, three, plan->d_tiles + lw.first,
-                          lw.count, ew, lw.flops, "tc_gemm:w") != cudaSuccess)
+                          plan->d_off + lw.off_first, lw.ctas, ew, lw.flops, "tc_gemm:w") != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, tc::MODE_X21, trans, unit, xp, 3, wp, 2, three, plan->d_tiles + lx.first,
-                          lx.count, ex, lx.flops, "tc_gemm:x21") != cudaSuccess)
+                          plan->d_off + lx.off_first, lx.ctas, ex, lx.flops, "tc_gemm:x21") != cudaSuccess)
             return TRI_ERR_CUDA;
     }
     // 5. Newton-Schulz: R = I - T X, then X += X R
     const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
     tc::Epi er{nullptr, 0, R[0], R[1], nullptr, L.ldp, n, n};
     if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
-                      plan->res.count, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
+                      plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
         return TRI_ERR_CUDA;
     const tc::Plane rp[2] = {pl(R[0], n, n, L.ldp), pl(R[1], n, n, L.ldp)};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
     if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 2, rp, 2, three, plan->d_tiles + plan->upd.first,
-                      plan->upd.count, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
+                      plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
         return TRI_ERR_CUDA;
     return TRI_OK;
 }

@@ -16,7 +16,7 @@
 namespace triinv {
 namespace {
 
-constexpr int TS = 32;   // transpose tile
+constexpr int TS = 64;   // tile edge; 256 threads, each thread two rows of a column at a time
 
 __device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
     h = __float2bfloat16_rn(v);
@@ -25,44 +25,77 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
     l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
-// One 32x32 tile (ti, tj) per CTA (blockIdx.x = ti, blockIdx.y = tj), 32x8 threads.
-// DIAG_ONLY: only tiles inside the diagonal 256-blocks are processed.
+// One 64 x 64 tile per CTA.  DIAG_ONLY: blockIdx.z is the diagonal 256-block and
+// (blockIdx.x, blockIdx.y) the tile inside it; otherwise (blockIdx.x, blockIdx.y) is the
+// tile of the whole matrix and tiles that no product reads return at once.
+// Thread t owns rows (2*(t%32), 2*(t%32)+1) of the tile and columns t/32 + 8*c, so a warp
+// stores 64 consecutive rows (128 bytes per plane) per column.
 template <bool TRANS, bool UNIT, bool DIAG_ONLY>
 __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a, int64_t lda, int64_t n,
                                                     __nv_bfloat16 *__restrict__ p0,
                                                     __nv_bfloat16 *__restrict__ p1,
                                                     __nv_bfloat16 *__restrict__ p2, int64_t ldp) {
-    const int64_t i0 = (int64_t)blockIdx.x * TS;   // rows
-    const int64_t j0 = (int64_t)blockIdx.y * TS;   // cols
-    if (i0 >= n || j0 >= n) return;
-    const bool diag_block = (i0 / 256) == (j0 / 256);
-    if (DIAG_ONLY && !diag_block) return;
-    if (!diag_block && j0 > i0) return;            // strictly upper block: never read
-    __shared__ float tile[TS][TS + 1];             // tile[i - i0][j - j0]
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    // Load (only the referenced triangle; the rest reads as 0, a unit diagonal as 1).
-    for (int r = ty; r < TS; r += 8) {
-        int64_t i, j;
-        if (TRANS) { i = i0 + r; j = j0 + tx; }    // contiguous along j
-        else { i = i0 + tx; j = j0 + r; }          // contiguous along i
-        float v = 0.f;
-        if (i < n && j < n) {
-            if (j < i) v = a[vidx<TRANS>(i, j, lda)];
-            else if (j == i) v = UNIT ? 1.f : a[vidx<TRANS>(i, i, lda)];
-        }
-        if (TRANS) tile[r][tx] = v;
-        else tile[tx][r] = v;
+    int64_t i0, j0;
+    if (DIAG_ONLY) {
+        i0 = (int64_t)blockIdx.z * 256 + blockIdx.x * TS;
+        j0 = (int64_t)blockIdx.z * 256 + blockIdx.y * TS;
+    } else {
+        i0 = (int64_t)blockIdx.x * TS;
+        j0 = (int64_t)blockIdx.y * TS;
+        const bool diag_block = (i0 / 256) == (j0 / 256);
+        if (!diag_block && j0 > i0) return;        // strictly upper block: never read
     }
-    __syncthreads();
-    for (int r = ty; r < TS; r += 8) {
-        const int64_t i = i0 + tx, j = j0 + r;
-        if (i >= n || j >= n) continue;
-        __nv_bfloat16 h, m, l;
-        split3(tile[tx][r], h, m, l);
-        const int64_t o = i + j * ldp;
-        p0[o] = h;
-        p1[o] = m;
-        p2[o] = l;
+    if (i0 >= n || j0 >= n) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // Referenced triangle only; the rest reads as 0 and a unit diagonal as 1.
+    auto fetch = [&](int64_t i, int64_t j) -> float {
+        if (i >= n || j >= n || j > i) return 0.f;
+        if (j == i) return UNIT ? 1.f : a[vidx<TRANS>(i, i, lda)];
+        return a[vidx<TRANS>(i, j, lda)];
+    };
+    if (TRANS) {
+        // The source is contiguous along j: stage the tile through shared memory.
+        __shared__ float tile[TS][TS + 1];         // tile[i - i0][j - j0]
+        for (int e = threadIdx.x; e < TS * TS; e += 256) {
+            const int ii = e / TS, jj = e % TS;
+            tile[ii][jj] = fetch(i0 + ii, j0 + jj);
+        }
+        __syncthreads();
+        for (int c = w; c < TS; c += 8) {
+            const int64_t j = j0 + c;
+            const int64_t i = i0 + 2 * lane;
+            if (j >= n || i >= n) continue;
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(tile[2 * lane][c], h0, m0, l0);
+            split3(tile[2 * lane + 1][c], h1, m1, l1);
+            const int64_t o = i + j * ldp;
+            if (i + 1 < n && !(o & 1)) {
+                *(__nv_bfloat162 *)(p0 + o) = __halves2bfloat162(h0, h1);
+                *(__nv_bfloat162 *)(p1 + o) = __halves2bfloat162(m0, m1);
+                *(__nv_bfloat162 *)(p2 + o) = __halves2bfloat162(l0, l1);
+            } else {
+                p0[o] = h0; p1[o] = m0; p2[o] = l0;
+                if (i + 1 < n) { p0[o + 1] = h1; p1[o + 1] = m1; p2[o + 1] = l1; }
+            }
+        }
+    } else {
+        for (int c = w; c < TS; c += 8) {
+            const int64_t j = j0 + c;
+            const int64_t i = i0 + 2 * lane;
+            if (j >= n || i >= n) continue;
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(fetch(i, j), h0, m0, l0);
+            split3(fetch(i + 1, j), h1, m1, l1);
+            const int64_t o = i + j * ldp;
+            if (i + 1 < n && !(o & 1)) {
+                *(__nv_bfloat162 *)(p0 + o) = __halves2bfloat162(h0, h1);
+                *(__nv_bfloat162 *)(p1 + o) = __halves2bfloat162(m0, m1);
+                *(__nv_bfloat162 *)(p2 + o) = __halves2bfloat162(l0, l1);
+            } else {
+                p0[o] = h0; p1[o] = m0; p2[o] = l0;
+                if (i + 1 < n) { p0[o + 1] = h1; p1[o + 1] = m1; p2[o + 1] = l1; }
+            }
+        }
     }
 }
 
@@ -73,7 +106,7 @@ cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_o
                                 __nv_bfloat16 *p2, int64_t ldp) {
     const int64_t t = (n + TS - 1) / TS;
     if (t <= 0) return cudaSuccess;
-    dim3 grid((unsigned)t, (unsigned)t);
+    dim3 grid = diag_only ? dim3(256 / TS, 256 / TS, (unsigned)((n + 255) / 256)) : dim3((unsigned)t, (unsigned)t);
     const double elems = diag_only ? (double)n * 256.0 : (double)n * n / 2.0;
     TraceScope ts(c.stream, diag_only ? "split_diag" : "split_t", 0.0, elems * (4.0 + 6.0));
 #define TRI_SPLIT(TR, UN, DO) split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp)

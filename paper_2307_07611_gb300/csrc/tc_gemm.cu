@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -242,6 +243,35 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
     }
 }
 
+// X values of row gm, columns gn0..gn0+15, that the update touches (lower triangle,
+// and the diagonal unless unit); others read as 0 and are not stored.
+template <bool TRANS, bool UNIT>
+__device__ __forceinline__ void load_x16(const Epi &ep, int64_t gm, int64_t gn0, float (&xv)[16]) {
+    int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+    const int64_t xstep = TRANS ? 1 : ep.ldx;
+    const bool row_ok = gm < ep.mlim;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int64_t gn = gn0 + j;
+        xv[j] = (row_ok && gn < ep.nlim && (gm > gn || (!UNIT && gm == gn))) ? ep.x[xo] : 0.f;
+        xo += xstep;
+    }
+}
+
+template <bool TRANS, bool UNIT>
+__device__ __forceinline__ void store_upd16(const Epi &ep, int64_t gm, int64_t gn0, const float (&xv)[16],
+                                            const uint32_t (&r)[16]) {
+    if (gm >= ep.mlim) return;
+    int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+    const int64_t xstep = TRANS ? 1 : ep.ldx;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int64_t gn = gn0 + j;
+        if (gn < ep.nlim && (gm > gn || (!UNIT && gm == gn))) ep.x[xo] = xv[j] + __uint_as_float(r[j]);
+        xo += xstep;
+    }
+}
+
 // Number of k-blocks accumulated in tensor memory before the epilogue adds them into
 // FP32 registers (MODE_RES only).  The tensor-core accumulator truncates each add, so a
 // long accumulation drifts towards zero by up to one unit in the last place per MMA; a
@@ -251,7 +281,8 @@ constexpr int kPromoteBlocks = 4;
 template <int MODE, bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
-               const Tile *__restrict__ tiles, const int ntiles, const Epi ep, int *gtimeout) {
+               const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
+               int *gtimeout) {
     constexpr bool PROMOTE = (MODE == MODE_RES);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -302,6 +333,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    const int t_begin = cta_off[blockIdx.x], t_end = cta_off[blockIdx.x + 1];
 
     if (warp == 0) {
         if (lane == 0) {
@@ -309,7 +341,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
             // Order: chunk, then term from the smallest pieces to hi*hi, then k-block.
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = t_begin; t < t_end && ok; ++t) {
                 const Tile tl = tiles[t];
                 const int cb = chunk_blocks(tl);
                 for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb) {
@@ -347,7 +379,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
             // ---------------- MMA issuer ----------------
             uint32_t it = 0, lc = 0;
             bool ok = true, issued = false;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = t_begin; t < t_end && ok; ++t) {
                 const Tile tl = tiles[t];
                 const int cb = chunk_blocks(tl);
                 for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb, ++lc) {
@@ -401,7 +433,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
         const int row = quarter * 32 + lane;
         uint32_t lc = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int t = t_begin; t < t_end && ok; ++t) {
             const Tile tl = tiles[t];
             const int cb = chunk_blocks(tl);
             const int64_t gm = (int64_t)tl.om + row;
@@ -410,6 +442,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
 #pragma unroll
                 for (int i = 0; i < BN / 2; ++i) sum[i] = 0.f;
             }
+            // The update reads X: fetch the first 16 columns before the accumulator is ready.
+            const int64_t gcol0 = (int64_t)tl.on + half * (BN / 2);
+            float xv[MODE == MODE_UPD ? 16 : 1];
+            if (MODE == MODE_UPD) load_x16<TRANS, UNIT>(ep, gm, gcol0, *(float(*)[16])xv);
             for (int c0 = tl.kb0; c0 < tl.kb1; c0 += cb, ++lc) {
                 const uint32_t a = lc & 1u, use = lc >> 1;
                 if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
@@ -427,12 +463,28 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
 #pragma unroll
                         for (int i = 0; i < 16; ++i) sum[q * 16 + i] += __uint_as_float(r[i]);
                     }
+                } else if (MODE == MODE_UPD) {
+                    // Software pipeline: the next 16 X values are in flight while the
+                    // current ones are added and stored.
+#pragma unroll 1
+                    for (int q = 0; q < BN / 32; ++q) {
+                        float xn[16];
+                        if (q + 1 < BN / 32)
+                            load_x16<TRANS, UNIT>(ep, gm, gcol0 + (q + 1) * 16, xn);
+                        uint32_t r[16];
+                        tmem_ld16(taddr + q * 16, r);
+                        store_upd16<TRANS, UNIT>(ep, gm, gcol0 + q * 16, *(float(*)[16])xv, r);
+                        if (q + 1 < BN / 32) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) xv[i] = xn[i];
+                        }
+                    }
                 } else {
 #pragma unroll 1
                     for (int q = 0; q < BN / 16; ++q) {
                         uint32_t r[8];
                         tmem_ld8(taddr + q * 8, r);
-                        epilogue_cols<MODE, TRANS, UNIT, 8>(ep, gm, (int64_t)tl.on + half * (BN / 2) + q * 8, r);
+                        epilogue_cols<MODE, TRANS, UNIT, 8>(ep, gm, gcol0 + q * 8, r);
                     }
                 }
                 tc_fence_before();
@@ -495,7 +547,7 @@ bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols) {
 
 template <int MODE, bool TRANS, bool UNIT>
 cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Tile *d_tiles,
-                     int ntiles, const Epi &epi) {
+                     const int *d_off, int ctas, const Epi &epi) {
     auto kern = tc_gemm_kernel<MODE, TRANS, UNIT>;
     static bool attr_set[64] = {};
     if (!attr_set[c.device]) {
@@ -503,17 +555,54 @@ cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const T
         if (e != cudaSuccess) return e;
         attr_set[c.device] = true;
     }
-    const int grid = ntiles < c.sm_count ? ntiles : c.sm_count;
-    kern<<<grid, NTHREADS, SMEM_BYTES, c.stream>>>(maps, terms, d_tiles, ntiles, epi, c.timeout);
+    kern<<<ctas, NTHREADS, SMEM_BYTES, c.stream>>>(maps, terms, d_tiles, d_off, epi, c.timeout);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int> &offsets) {
+    const int nt = (int)tiles.size();
+    if (ctas > nt) ctas = nt;
+    if (ctas < 1) ctas = 1;
+    constexpr int kEpilogueCost = 8;   // pipeline-slot equivalents per tile
+    auto cost = [&](const Tile &t) { return (t.kb1 - t.kb0) * terms + kEpilogueCost; };
+    std::vector<int> order(nt);
+    for (int i = 0; i < nt; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return cost(tiles[x]) > cost(tiles[y]); });
+    // min-heap of (load, cta)
+    std::vector<std::pair<long long, int>> heap;
+    for (int b = 0; b < ctas; ++b) heap.push_back({0, b});
+    auto cmp = [](const std::pair<long long, int> &x, const std::pair<long long, int> &y) {
+        return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    std::vector<std::vector<int>> lists(ctas);
+    for (int i : order) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto &top = heap.back();
+        lists[top.second].push_back(i);
+        top.first += cost(tiles[i]);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<Tile> out;
+    out.reserve(nt);
+    offsets.assign(ctas + 1, 0);
+    for (int b = 0; b < ctas; ++b) {
+        offsets[b] = (int)out.size();
+        for (int i : lists[b]) out.push_back(tiles[i]);
+    }
+    offsets[ctas] = (int)out.size();
+    tiles.swap(out);
+    return ctas;
+}
+
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes, int na,
                       const Plane *bplanes, int nb, const Terms &terms, const Tile *d_tiles,
-                      int ntiles, const Epi &epi, double flops, const char *trace_name) {
-    if (ntiles <= 0) return cudaSuccess;
+                      const int *d_off, int ctas, const Epi &epi, double flops,
+                      const char *trace_name) {
+    if (ctas <= 0) return cudaSuccess;
     if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
     Maps maps;
     memset(&maps, 0, sizeof(maps));
@@ -526,17 +615,17 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     TraceScope ts(c.stream, trace_name, flops, 0.0);
 #define TRI_TC_CASE(M)                                                                   \
     case M:                                                                              \
-        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, d_tiles, ntiles, epi)   \
-                               : launch_t<M, true, false>(c, maps, terms, d_tiles, ntiles, epi); \
-        return unit ? launch_t<M, false, true>(c, maps, terms, d_tiles, ntiles, epi)             \
-                    : launch_t<M, false, false>(c, maps, terms, d_tiles, ntiles, epi);
+        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, d_tiles, d_off, ctas, epi)   \
+                               : launch_t<M, true, false>(c, maps, terms, d_tiles, d_off, ctas, epi); \
+        return unit ? launch_t<M, false, true>(c, maps, terms, d_tiles, d_off, ctas, epi)             \
+                    : launch_t<M, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
     switch (mode) {
         TRI_TC_CASE(MODE_W)
         TRI_TC_CASE(MODE_X21)
         TRI_TC_CASE(MODE_RES)
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:
-            return launch_t<MODE_F32, false, false>(c, maps, terms, d_tiles, ntiles, epi);
+            return launch_t<MODE_F32, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
         default:
             return cudaErrorInvalidValue;
     }
@@ -572,17 +661,22 @@ extern "C" tri_status tri_tc_gemm_bf16(int64_t m, int64_t n, int64_t k, int nter
         for (int64_t tn = 0; tn * tc::BN < n; ++tn)
             v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), 0, (int)kb, (int)(tm * tc::BM),
                                  (int)(tn * tc::BN)});
-    tc::Tile *d = nullptr;
-    const size_t bytes = v.size() * sizeof(tc::Tile);
-    if (cudaMallocAsync((void **)&d, bytes, ctx.stream) != cudaSuccess) {
+    std::vector<int> off;
+    const int ctas = tc::schedule_lpt(v, nterms, ctx.sm_count, off);
+    const size_t tbytes = v.size() * sizeof(tc::Tile), obytes = off.size() * sizeof(int);
+    uint8_t *d = nullptr;
+    if (cudaMallocAsync((void **)&d, tbytes + obytes, ctx.stream) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
-    if (cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, ctx.stream) != cudaSuccess) return TRI_ERR_CUDA;
+    if (cudaMemcpyAsync(d, v.data(), tbytes, cudaMemcpyHostToDevice, ctx.stream) != cudaSuccess ||
+        cudaMemcpyAsync(d + tbytes, off.data(), obytes, cudaMemcpyHostToDevice, ctx.stream) != cudaSuccess)
+        return TRI_ERR_CUDA;
     tc::Terms terms{nterms, {0, 1, 2}, {0, 1, 2}};
     tc::Epi ep{c, ldc, nullptr, nullptr, nullptr, 0, m, n};
-    cudaError_t e = tc::launch_tc(ctx, tc::MODE_F32, false, false, ap, nterms, bp, nterms, terms, d,
-                                  (int)v.size(), ep, 2.0 * m * n * k * nterms, "tc_gemm:f32");
+    cudaError_t e = tc::launch_tc(ctx, tc::MODE_F32, false, false, ap, nterms, bp, nterms, terms,
+                                  (const tc::Tile *)d, (const int *)(d + tbytes), ctas, ep,
+                                  2.0 * m * n * k * nterms, "tc_gemm:f32");
     cudaFreeAsync(d, ctx.stream);
     return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }

@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "internal.cuh"
 
 namespace triinv {
@@ -50,12 +52,19 @@ struct Plane {
     int64_t rows, cols, ld;
 };
 
-// Encodes the tensor maps, then launches the persistent kernel over `ntiles` tiles read
-// from device memory.  amaps/bmaps: up to 3 planes each, indexed by `terms`.
+// Greedy longest-processing-time assignment of tiles to `ctas` persistent CTAs: tiles are
+// reordered so that CTA b owns [offsets[b], offsets[b+1]), each list longest first.  The
+// cost of a tile is its number of pipeline slots (k-blocks x terms) plus a fixed
+// epilogue cost.  Returns the number of CTAs that received work.
+int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int> &offsets);
+
+// Encodes the tensor maps, then launches `ctas` persistent CTAs; CTA b processes the
+// tiles d_tiles[d_off[b] .. d_off[b+1]).  aplanes/bplanes: up to 3 planes each, indexed
+// by `terms`.
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
                       int na, const Plane *bplanes, int nb, const Terms &terms,
-                      const Tile *d_tiles, int ntiles, const Epi &epi, double flops,
-                      const char *trace_name);
+                      const Tile *d_tiles, const int *d_off, int ctas, const Epi &epi,
+                      double flops, const char *trace_name);
 
 }  // namespace tc
 }  // namespace triinv
