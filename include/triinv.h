@@ -101,6 +101,27 @@ TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, 
                       tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * General inverse, in place: A <- A^-1 for a dense n x n matrix, as A^-1 = U^-1 L^-1 from
+ * an unpivoted block LU (BRSI with two blocks reduced to the Schur complement, Section
+ * 5.2; inverse factors S = U^-1, K = L^-1 formed alongside the factorisation as in SKUL,
+ * Section 5.1, "S K = A^-1").  Intended for matrices that need no pivoting (e.g. diagonally
+ * dominant ones); a zero or non-finite pivot is recorded and reported by tri_get_info.
+ *   n     order, n >= 0;  a: device pointer, lda x n column-major;  lda >= max(1, n).
+ *   dtype TRI_F64 (DFMA), TRI_F32 (FFMA) or TRI_F32_MIXED (split-BF16 tensor-core
+ *         products with three terms and FP32 accumulation, FP32 leaves).
+ * Errors: TRI_ERR_ARG, TRI_ERR_NOMEM (scratch), TRI_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream);
+
+/* Bytes of 256-byte aligned device scratch gen_inv_ex needs (about 2 n^2 elements, plus
+ * the BF16 operand planes of the largest product for TRI_F32_MIXED). */
+TRI_API size_t gen_inv_workspace_size(int64_t n, tri_dtype dtype);
+
+/* gen_inv with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+TRI_API tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *workspace,
+                              size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * tri_inv_noalloc -- tri_inv for callers that cannot allocate device memory.
  * The paper has no counterpart; this is an integration entry point.
  *

@@ -167,6 +167,8 @@ tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, i
 }
 
 size_t mixed_ws_bytes(int64_t n);
+size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt);
+tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws);
 tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws);
 
 }  // namespace triinv
@@ -235,6 +237,45 @@ tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda
         cudaError_t e = cudaFreeAsync(ws, s);
         if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     }
+    return st;
+}
+
+size_t gen_inv_workspace_size(int64_t n, tri_dtype dtype) {
+    if (n <= 0 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
+    return gen_inv_ws_bytes(n, dtype);
+}
+
+tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *workspace, size_t ws_bytes,
+                      void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    if (n > (int64_t)1 << 30) return TRI_ERR_UNSUPPORTED;
+    const size_t need = gen_inv_ws_bytes(n, dtype);
+    if (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)) return TRI_ERR_NOMEM;
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    return run_gen_inv(c, dtype, n, a, lda, workspace);
+}
+
+tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(s, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = gen_inv_ws_bytes(n, dtype);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = gen_inv_ex(n, a, lda, dtype, ws, need, stream);
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
 }
 

@@ -1,0 +1,43 @@
+// gemm.cuh -- the generic triangular-aware product used by the general inverse and the
+// adjoint: C = alpha * A * B + beta * C, column-major, operands full or triangular.
+#pragma once
+
+#include "internal.cuh"
+
+namespace triinv {
+
+enum OpKind {
+    OP_FULL = 0,
+    OP_LOWER = 1,
+    OP_UPPER = 2,
+    OP_LOWER_UNIT = 3,   // strict lower part stored, diagonal taken as 1
+    OP_UPPER_UNIT = 4,
+};
+
+struct GemmArgs {
+    int64_t m, n, k;
+    double alpha;
+    const void *a;
+    int64_t lda;
+    int akind;
+    const void *b;
+    int64_t ldb;
+    int bkind;
+    double beta;
+    void *c;
+    int64_t ldc;
+    int cmask;   // OP_FULL, OP_LOWER or OP_UPPER: which part of C is written
+};
+
+double gemm_flops(const GemmArgs &g);
+
+// CUDA-core product (FP32 or FP64 by dt).
+cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name);
+
+// Split-BF16 tensor-core product (FP32 data): both operands are split into BF16
+// hi/mid planes inside `ws` and `terms` (1, 3 or 6) pieces are accumulated in FP32.
+// ws must hold gemm_tc_ws_bytes(m, n, k) bytes.
+size_t gemm_tc_ws_bytes(int64_t m, int64_t n, int64_t k);
+cudaError_t gemm_tc(const Ctx &c, const GemmArgs &g, int terms, void *ws, const char *trace_name);
+
+}  // namespace triinv

@@ -1,0 +1,179 @@
+// gemm_simt.cu -- generic triangular-aware product on CUDA cores (FP32 FFMA / FP64 DFMA):
+//     C = alpha * A * B + beta * C
+// with A (M x K), B (K x N), C (M x N) column-major and each operand full, lower or upper
+// triangular (optionally with an implicit unit diagonal).  The zero part of a triangular
+// operand is skipped through the k range of each tile and never loaded.  Used by the
+// general inverse (block LU with inverse factors, then U^-1 L^-1) and by the adjoint.
+#include <algorithm>
+
+#include "gemm.cuh"
+
+namespace triinv {
+namespace {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+struct GCfg {
+    static constexpr int NT = (BM / TM) * (BN / TN);
+    static constexpr int PAD = 4;
+    static constexpr int A_PER = BM * BK / NT;
+    static constexpr int B_PER = BN * BK / NT;
+};
+
+template <int BX, int TX>
+__device__ __forceinline__ int gmicro(int t, int r) {
+    if (TX == 8) return (r < 4) ? (t * 4 + r) : (BX / 2 + t * 4 + (r - 4));
+    return t * TX + r;
+}
+
+// Element (r, c) of a triangular-kind operand; rows/cols are the operand's own indices.
+template <typename T>
+__device__ __forceinline__ T tri_fetch(const T *p, int64_t ld, int kind, int64_t r, int64_t c) {
+    switch (kind) {
+        case OP_FULL: return p[r + c * ld];
+        case OP_LOWER: return c <= r ? p[r + c * ld] : T(0);
+        case OP_UPPER: return c >= r ? p[r + c * ld] : T(0);
+        case OP_LOWER_UNIT: return c < r ? p[r + c * ld] : (c == r ? T(1) : T(0));
+        case OP_UPPER_UNIT: return c > r ? p[r + c * ld] : (c == r ? T(1) : T(0));
+    }
+    return T(0);
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(GCfg<T, BM, BN, BK, TM, TN>::NT)
+gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__ A, int64_t lda,
+                 int akind, const T *__restrict__ B, int64_t ldb, int bkind, T beta, T *C,
+                 int64_t ldc, int cmask) {
+    using Cf = GCfg<T, BM, BN, BK, TM, TN>;
+    constexpr int NT = Cf::NT;
+    __shared__ __align__(16) T As[2][BK][BM + Cf::PAD];
+    __shared__ __align__(16) T Bs[2][BK][BN + Cf::PAD];
+    const int tid = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.y * BM;
+    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    if (m0 >= M || n0 >= N) return;
+    // Output mask: skip tiles entirely outside the stored triangle.
+    if (cmask == OP_LOWER && n0 > m0 + BM - 1) return;
+    if (cmask == OP_UPPER && m0 > n0 + BN - 1) return;
+
+    int64_t kbeg = 0, kend = K;
+    const bool a_low = (akind == OP_LOWER || akind == OP_LOWER_UNIT);
+    const bool a_up = (akind == OP_UPPER || akind == OP_UPPER_UNIT);
+    const bool b_low = (bkind == OP_LOWER || bkind == OP_LOWER_UNIT);
+    const bool b_up = (bkind == OP_UPPER || bkind == OP_UPPER_UNIT);
+    if (a_low) kend = min(kend, m0 + BM);          // A(m,k) = 0 for k > m
+    if (a_up) kbeg = max(kbeg, (m0 / BK) * BK);    // A(m,k) = 0 for k < m
+    if (b_low) kbeg = max(kbeg, (n0 / BK) * BK);   // B(k,n) = 0 for k < n
+    if (b_up) kend = min(kend, n0 + BN);           // B(k,n) = 0 for k > n
+
+    T ra[Cf::A_PER], rb[Cf::B_PER];
+    auto gload = [&](int64_t kt) {
+#pragma unroll
+        for (int r = 0; r < Cf::A_PER; ++r) {
+            const int idx = tid + r * NT;
+            const int m = idx % BM, k = idx / BM;
+            const int64_t gm = m0 + m, gk = kt + k;
+            ra[r] = (gm < M && gk < kend) ? tri_fetch(A, lda, akind, gm, gk) : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < Cf::B_PER; ++r) {
+            const int idx = tid + r * NT;
+            const int k = idx % BK, nn = idx / BK;
+            const int64_t gk = kt + k, gn = n0 + nn;
+            rb[r] = (gn < N && gk < kend) ? tri_fetch(B, ldb, bkind, gk, gn) : T(0);
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < Cf::A_PER; ++r) {
+            const int idx = tid + r * NT;
+            As[buf][idx / BM][idx % BM] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < Cf::B_PER; ++r) {
+            const int idx = tid + r * NT;
+            Bs[buf][idx % BK][idx / BK] = rb[r];
+        }
+    };
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    int buf = 0;
+    if (kbeg < kend) {
+        gload(kbeg);
+        sstore(0);
+        __syncthreads();
+    }
+    for (int64_t kt = kbeg; kt < kend; kt += BK) {
+        const bool more = kt + BK < kend;
+        if (more) gload(kt + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T fa[TM], fb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) fa[i] = As[buf][kk][gmicro<BM, TM>(ty, i)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) fb[j] = Bs[buf][kk][gmicro<BN, TN>(tx, j)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(fa[i], fb[j], acc[i][j]);
+        }
+        if (more) {
+            sstore(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t gm = m0 + gmicro<BM, TM>(ty, i);
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t gn = n0 + gmicro<BN, TN>(tx, j);
+            if (gn >= N) continue;
+            if (cmask == OP_LOWER && gn > gm) continue;
+            if (cmask == OP_UPPER && gm > gn) continue;
+            T *c = C + gm + gn * ldc;
+            *c = beta == T(0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+        }
+    }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_g(const Ctx &c, const GemmArgs &g) {
+    using Cf = GCfg<T, BM, BN, BK, TM, TN>;
+    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM));
+    gemm_simt_kernel<T, BM, BN, BK, TM, TN><<<grid, Cf::NT, 0, c.stream>>>(
+        g.m, g.n, g.k, (T)g.alpha, (const T *)g.a, g.lda, g.akind, (const T *)g.b, g.ldb, g.bkind,
+        (T)g.beta, (T *)g.c, g.ldc, g.cmask);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+double gemm_flops(const GemmArgs &g) {
+    // 2 x the multiply-adds that are not structurally zero.
+    const double M = (double)g.m, N = (double)g.n, K = (double)g.k;
+    const bool a_tri = g.akind != OP_FULL, b_tri = g.bkind != OP_FULL;
+    if (!a_tri && !b_tri) return 2.0 * M * N * K;
+    if (a_tri && !b_tri) return M * (M + 1) * N;           // square triangular A (M == K)
+    if (!a_tri && b_tri) return M * N * (N + 1);           // square triangular B (N == K)
+    const bool a_low = g.akind == OP_LOWER || g.akind == OP_LOWER_UNIT;
+    const bool b_low = g.bkind == OP_LOWER || g.bkind == OP_LOWER_UNIT;
+    if (a_low == b_low) return M * (M + 1) * (M + 2) / 3.0;  // triangular result
+    return M * (M + 1) * (2 * M + 1) / 3.0;                 // upper x lower or lower x upper
+}
+
+cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name) {
+    if (g.m <= 0 || g.n <= 0) return cudaSuccess;
+    TraceScope ts(c.stream, trace_name, gemm_flops(g), 0.0);
+    if (dt == TRI_F64) return launch_g<double, 64, 64, 16, 4, 4>(c, g);
+    if (g.m >= 128 && g.n >= 128) return launch_g<float, 128, 128, 8, 8, 8>(c, g);
+    return launch_g<float, 64, 64, 16, 4, 4>(c, g);
+}
+
+}  // namespace triinv

@@ -1,0 +1,264 @@
+// gen_inv.cu -- a5: general inverse A^-1 = U^-1 L^-1 from an unpivoted block LU.
+//
+// The factorisation and the inverse factors are built together, block-recursively, in
+// the spirit of SKUL (Section 5.1: "S K = A^-1", the inverse factors S = U^-1 and
+// K = L^-1 formed alongside L and U) and of the 2-block split of BRSI (Section 5.2, the
+// Schur-complement form).  For A = [A11 A12; A21 A22] (Doolittle: L unit lower):
+//     (K11, S11) = rec(A11)
+//     U12 = K11 A12,   L21 = A21 S11,   A22 <- A22 - L21 U12     (Schur complement)
+//     (K22, S22) = rec(A22)
+//     K21 = -K22 (L21 K11),   S12 = -(S11 U12) S22               (block inverses, Section 3)
+// and finally A^-1 = S K (upper times unit lower).  Leaves (128 x 128 in FP32, 64 x 64 in
+// FP64) are factored and inverted by one CTA in shared memory.  Flops: LU 2n^3/3, inverse
+// factors 2n^3/3, product 2n^3/3.
+//
+// K (strict lower, unit diagonal implied) and S (upper with diagonal) share one n x n
+// workspace buffer.  No pivoting: a zero or non-finite pivot is recorded and reported by
+// tri_get_info.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "gemm.cuh"
+
+namespace triinv {
+namespace {
+
+// Right-looking column recurrence on a lower view held in shared memory (the same sums as
+// the CRIT recurrence, Section 4.2): each thread keeps rows ig + r*G of column j of the
+// inverse in registers; one barrier per k.  get(i, k) reads the lower view.
+template <typename T, int L, int NT, bool UNIT, typename Get>
+__device__ __forceinline__ void lower_inverse_regs(Get get, int nb, T (&acc)[L * L / NT], T (*xrow)[L]) {
+    constexpr int G = NT / L;
+    constexpr int RPT = L * L / NT;
+    const int j = threadIdx.x % L, ig = threadIdx.x / L;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r] = T(0);
+    for (int k = 0; k < nb; ++k) {
+        const T dk = UNIT ? T(1) : T(1) / get(k, k);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int i = ig + r * G;
+            if (i == k && j <= k) {
+                const T x = (j == k) ? dk : -acc[r] * dk;
+                acc[r] = x;
+                xrow[k & 1][j] = x;
+            }
+        }
+        __syncthreads();
+        if (j <= k) {
+            const T xkj = xrow[k & 1][j];
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int i = ig + r * G;
+                if (i > k && i < nb) acc[r] = fma(get(i, k), xkj, acc[r]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One leaf block [off, off + nb) of A: unpivoted LU in shared memory, then
+// K = L^-1 (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
+template <typename T, int L, int NT>
+__global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *__restrict__ a, int64_t lda, T *__restrict__ ks,
+                                                     int64_t ldk, int64_t off, int nb, long long *info) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T (*s)[L + 1] = reinterpret_cast<T (*)[L + 1]>(smem_raw);
+    T (*xrow)[L] = reinterpret_cast<T (*)[L]>(smem_raw + sizeof(T) * L * (L + 1));
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < L * L; idx += NT) {
+        const int i = idx % L, j = idx / L;
+        T v = (i == j) ? T(1) : T(0);
+        if (i < nb && j < nb) v = a[(off + i) + (off + j) * lda];
+        s[i][j] = v;
+    }
+    __syncthreads();
+    // Doolittle LU, right-looking: column k of L, then the rank-1 Schur update.
+    for (int k = 0; k < nb; ++k) {
+        const T piv = s[k][k];
+        if (tid == 0 && (piv == T(0) || !isfinite(piv))) atomicMin(info, (long long)(off + k));
+        const T rp = T(1) / piv;
+        for (int i = k + 1 + tid; i < nb; i += NT) s[i][k] *= rp;
+        __syncthreads();
+        // Rank-1 update on a (NT/32) x 32 thread grid: rows step by NT/32, columns by 32.
+        for (int j = k + 1 + (tid >> 5); j < nb; j += NT / 32) {
+            const T ukj = s[k][j];
+            for (int i = k + 1 + (tid & 31); i < nb; i += 32) s[i][j] = fma(-s[i][k], ukj, s[i][j]);
+        }
+        __syncthreads();
+    }
+    constexpr int RPT = L * L / NT;
+    constexpr int G = NT / L;
+    const int j = tid % L, ig = tid / L;
+    T acc[RPT];
+    // K = L^-1: lower view of the strict lower part with a unit diagonal.
+    lower_inverse_regs<T, L, NT, true>([&](int i, int k) { return s[i][k]; }, nb, acc, xrow);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int i = ig + r * G;
+        if (i < nb && j < i) ks[(off + i) + (off + j) * ldk] = acc[r];
+    }
+    // S = U^-1 = ((U^T)^-1)^T: lower view U^T(i, k) = s[k][i].
+    lower_inverse_regs<T, L, NT, false>([&](int i, int k) { return s[k][i]; }, nb, acc, xrow);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        const int i = ig + r * G;
+        if (i < nb && j <= i) ks[(off + j) + (off + i) * ldk] = acc[r];
+    }
+}
+
+struct Node {
+    int64_t off, m1, m2;
+};
+
+int leaf_size(tri_dtype dt) { return dt == TRI_F64 ? 64 : 128; }
+size_t esz(tri_dtype dt) { return dt == TRI_F64 ? 8 : 4; }
+
+int64_t split_point(int64_t m, int L) {
+    const int64_t blocks = (m + L - 1) / L;
+    return (int64_t)L * ((blocks + 1) / 2);
+}
+
+// Temp sizes per recursion depth (elements): three buffers of m1 * m2 each.
+void depth_sizes(int64_t n, int L, std::vector<int64_t> &sz) {
+    sz.clear();
+    std::vector<int64_t> level{n};
+    while (true) {
+        int64_t best = 0;
+        std::vector<int64_t> next;
+        for (int64_t m : level) {
+            if (m <= L) continue;
+            const int64_t m1 = split_point(m, L), m2 = m - m1;
+            best = std::max(best, m1 * m2);
+            next.push_back(m1);
+            next.push_back(m2);
+        }
+        if (next.empty()) break;
+        sz.push_back(best);
+        level.swap(next);
+    }
+}
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+struct GenLayout {
+    size_t ks, temps, planes, total;
+    std::vector<size_t> depth_off;
+};
+
+GenLayout gen_layout(int64_t n, tri_dtype dt) {
+    GenLayout g{};
+    const int L = leaf_size(dt);
+    std::vector<int64_t> sz;
+    depth_sizes(n, L, sz);
+    g.ks = al((size_t)n * n * esz(dt));
+    size_t o = g.ks;
+    for (int64_t s : sz) {
+        g.depth_off.push_back(o);
+        o += 3 * al((size_t)s * esz(dt));
+    }
+    g.temps = o - g.ks;
+    g.planes = 0;
+    if (dt == TRI_F32_MIXED) g.planes = al(gemm_tc_ws_bytes(n, n, n));
+    g.total = o + g.planes;
+    return g;
+}
+
+struct GenCtx {
+    const Ctx *c;
+    tri_dtype dt;
+    uint8_t *ws;
+    GenLayout lay;
+    int L;
+};
+
+constexpr int64_t kTcMin = 512;   // smaller products stay on CUDA cores
+
+cudaError_t product(const GenCtx &g, const GemmArgs &a, const char *name) {
+    if (g.dt == TRI_F32_MIXED && a.m >= kTcMin && a.n >= kTcMin && a.k >= kTcMin)
+        return gemm_tc(*g.c, a, 3, g.ws + g.lay.ks + g.lay.temps, name);
+    return gemm_simt(*g.c, g.dt == TRI_F64 ? TRI_F64 : TRI_F32, a, name);
+}
+
+cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int64_t ldk, int64_t off, int nb) {
+    TraceScope ts(g.c->stream, g.dt == TRI_F64 ? "lu_leaf_f64" : "lu_leaf_f32",
+                  (double)nb * nb * nb * 4.0 / 3.0, 0.0);
+    if (g.dt == TRI_F64) {
+        constexpr int L = 64, NT = 256;
+        const size_t sm = sizeof(double) * (L * (L + 1) + 2 * L);
+        lu_leaf_kernel<double, L, NT><<<1, NT, sm, g.c->stream>>>((const double *)a, lda, (double *)ks, ldk,
+                                                                  off, nb, g.c->info);
+    } else {
+        constexpr int L = 128, NT = 1024;
+        const size_t sm = sizeof(float) * (L * (L + 1) + 2 * L);
+        cudaError_t e = cudaFuncSetAttribute(lu_leaf_kernel<float, L, NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        lu_leaf_kernel<float, L, NT><<<1, NT, sm, g.c->stream>>>((const float *)a, lda, (float *)ks, ldk, off,
+                                                                 nb, g.c->info);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t rec(const GenCtx &g, uint8_t *a, int64_t lda, uint8_t *ks, int64_t ldk, int64_t off, int64_t m,
+                int depth) {
+    const size_t es = esz(g.dt);
+    if (m <= g.L) return launch_leaf_lu(g, a, lda, ks, ldk, off, (int)m);
+    const int64_t m1 = split_point(m, g.L), m2 = m - m1;
+    cudaError_t e = rec(g, a, lda, ks, ldk, off, m1, depth + 1);
+    if (e != cudaSuccess) return e;
+    auto A = [&](int64_t i, int64_t j) { return (void *)(a + ((off + i) + (off + j) * lda) * es); };
+    auto KS = [&](int64_t i, int64_t j) { return (void *)(ks + ((off + i) + (off + j) * ldk) * es); };
+    uint8_t *tb = g.ws + g.lay.depth_off[depth];
+    const size_t tsz = al((size_t)m1 * m2 * es);
+    void *T1 = tb, *T2 = tb + tsz, *T3 = tb + 2 * tsz;
+    // U12 = K11 A12  (m1 x m2)
+    e = product(g, GemmArgs{m1, m2, m1, 1.0, KS(0, 0), ldk, OP_LOWER_UNIT, A(0, m1), lda, OP_FULL, 0.0, T1, m1,
+                            OP_FULL}, "gen:u12");
+    if (e != cudaSuccess) return e;
+    // L21 = A21 S11  (m2 x m1)
+    e = product(g, GemmArgs{m2, m1, m1, 1.0, A(m1, 0), lda, OP_FULL, KS(0, 0), ldk, OP_UPPER, 0.0, T2, m2,
+                            OP_FULL}, "gen:l21");
+    if (e != cudaSuccess) return e;
+    // A22 <- A22 - L21 U12
+    e = product(g, GemmArgs{m2, m2, m1, -1.0, T2, m2, OP_FULL, T1, m1, OP_FULL, 1.0, A(m1, m1), lda, OP_FULL},
+                "gen:schur");
+    if (e != cudaSuccess) return e;
+    e = rec(g, a, lda, ks, ldk, off + m1, m2, depth + 1);
+    if (e != cudaSuccess) return e;
+    // K21 = -K22 (L21 K11)
+    e = product(g, GemmArgs{m2, m1, m1, 1.0, T2, m2, OP_FULL, KS(0, 0), ldk, OP_LOWER_UNIT, 0.0, T3, m2,
+                            OP_FULL}, "gen:k21a");
+    if (e != cudaSuccess) return e;
+    e = product(g, GemmArgs{m2, m1, m2, -1.0, KS(m1, m1), ldk, OP_LOWER_UNIT, T3, m2, OP_FULL, 0.0, KS(m1, 0),
+                            ldk, OP_FULL}, "gen:k21b");
+    if (e != cudaSuccess) return e;
+    // S12 = -(S11 U12) S22
+    e = product(g, GemmArgs{m1, m2, m1, 1.0, KS(0, 0), ldk, OP_UPPER, T1, m1, OP_FULL, 0.0, T3, m1, OP_FULL},
+                "gen:s12a");
+    if (e != cudaSuccess) return e;
+    return product(g, GemmArgs{m1, m2, m2, -1.0, T3, m1, OP_FULL, KS(m1, m1), ldk, OP_UPPER, 0.0, KS(0, m1), ldk,
+                               OP_FULL}, "gen:s12b");
+}
+
+}  // namespace
+
+size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt) {
+    if (n <= 0) return 0;
+    return gen_layout(n, dt).total;
+}
+
+tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws) {
+    GenCtx g{&c, dt, (uint8_t *)ws, gen_layout(n, dt), leaf_size(dt)};
+    uint8_t *ks = (uint8_t *)ws;
+    const int64_t ldk = n;
+    cudaError_t e = rec(g, (uint8_t *)a, lda, ks, ldk, 0, n, 0);
+    if (e != cudaSuccess) return TRI_ERR_CUDA;
+    // A^-1 = S K
+    e = product(g, GemmArgs{n, n, n, 1.0, ks, ldk, OP_UPPER, ks, ldk, OP_LOWER_UNIT, 0.0, a, lda, OP_FULL},
+                "gen:sk");
+    return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+}  // namespace triinv

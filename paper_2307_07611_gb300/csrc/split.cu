@@ -99,7 +99,57 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
     }
 }
 
+// Rectangle rows x cols (column-major, lds) -> planes, with the triangle kind of the
+// operand applied (0 outside the stored triangle, 1 on an implicit unit diagonal).
+// Thread t owns rows 2*(t%32), 2*(t%32)+1 of a 64-row strip; blockIdx.y = 8-column group.
+__global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict__ a, int64_t lds,
+                                                         int64_t rows, int64_t cols, int kind,
+                                                         __nv_bfloat16 *__restrict__ p0,
+                                                         __nv_bfloat16 *__restrict__ p1,
+                                                         __nv_bfloat16 *__restrict__ p2, int64_t ldp) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 64 + 2 * lane;
+    const int64_t j = (int64_t)blockIdx.y * 8 + w;
+    if (i >= rows || j >= cols) return;
+    auto fetch = [&](int64_t r) -> float {
+        if (r >= rows) return 0.f;
+        switch (kind) {
+            case 1: return j <= r ? a[r + j * lds] : 0.f;                        // lower
+            case 2: return j >= r ? a[r + j * lds] : 0.f;                        // upper
+            case 3: return j < r ? a[r + j * lds] : (j == r ? 1.f : 0.f);        // lower, unit
+            case 4: return j > r ? a[r + j * lds] : (j == r ? 1.f : 0.f);        // upper, unit
+            default: return a[r + j * lds];
+        }
+    };
+    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+    split3(fetch(i), h0, m0, l0);
+    split3(fetch(i + 1), h1, m1, l1);
+    const int64_t o = i + j * ldp;
+    if (i + 1 < rows && !(o & 1)) {
+        *(__nv_bfloat162 *)(p0 + o) = __halves2bfloat162(h0, h1);
+        *(__nv_bfloat162 *)(p1 + o) = __halves2bfloat162(m0, m1);
+        if (p2) *(__nv_bfloat162 *)(p2 + o) = __halves2bfloat162(l0, l1);
+    } else {
+        p0[o] = h0; p1[o] = m0;
+        if (p2) p2[o] = l0;
+        if (i + 1 < rows) {
+            p0[o + 1] = h1; p1[o + 1] = m1;
+            if (p2) p2[o + 1] = l1;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t rows, int64_t cols,
+                              int kind, __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
+                              int64_t ldp) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((cols + 7) / 8));
+    TraceScope ts(c.stream, "split_rect", 0.0, (double)rows * cols * (4.0 + (p2 ? 6.0 : 4.0)));
+    split_rect_kernel<<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,

@@ -233,6 +233,18 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
             if (j < left && (gm > gn || (!UNIT && gm == gn))) ep.x[xo] += __uint_as_float(r[j]);
             xo += xstep;
         }
+    } else if (MODE == MODE_GEN) {
+        int64_t xo = gm + gn0 * ep.ldx;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const int64_t gn = gn0 + j;
+            const bool keep = j < left && !(ep.cmask == 1 && gn > gm) && !(ep.cmask == 2 && gm > gn);
+            if (keep) {
+                const float v = ep.alpha * __uint_as_float(r[j]);
+                ep.x[xo] = ep.beta == 0.f ? v : fmaf(ep.beta, ep.x[xo], v);
+            }
+            xo += ep.ldx;
+        }
     } else {
         int64_t xo = gm + gn0 * ep.ldx;
 #pragma unroll
@@ -626,6 +638,8 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:
             return launch_t<MODE_F32, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
+        case MODE_GEN:
+            return launch_t<MODE_GEN, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
         default:
             return cudaErrorInvalidValue;
     }

@@ -35,6 +35,8 @@ struct Epi {
     __nv_bfloat16 *o0, *o1, *o2;   // BF16 output planes, column-major, leading dim ldo
     int64_t ldo;
     int64_t mlim, nlim;            // output rows / columns that exist
+    float alpha = 1.f, beta = 0.f; // MODE_GEN: x <- alpha * acc + beta * x
+    int cmask = 0;                 // MODE_GEN: 0 full, 1 lower, 2 upper part of x written
 };
 
 enum Mode {
@@ -43,6 +45,7 @@ enum Mode {
     MODE_RES = 2,    // o0/o1 <- hi/lo split of I - acc (lower), 0 above    (R = I - T X)
     MODE_UPD = 3,    // x += acc on the lower triangle                       (X += X R)
     MODE_F32 = 4,    // x <- acc (plain column-major store, no view)        (verification)
+    MODE_GEN = 5,    // x <- alpha acc + beta x, column-major, masked        (general products)
 };
 
 // A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld

@@ -45,6 +45,9 @@ def _declare(lib):
         "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
+        "gen_inv": ([i64, vp, i64, i32, vp], i32),
+        "gen_inv_workspace_size": ([i64, i32], sz),
+        "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
                               vp, i64, vp], i32),
         "tri_trace_enable": ([i32], None),
@@ -95,6 +98,18 @@ def tri_inv_workspace_size(n, dtype) -> int:
 def tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
     return load().tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace or None, ws_bytes,
                              stream or None)
+
+
+def gen_inv(n, ptr, ld, dtype, stream=0) -> int:
+    return load().gen_inv(n, ptr, ld, dtype, stream or None)
+
+
+def gen_inv_workspace_size(n, dtype) -> int:
+    return int(load().gen_inv_workspace_size(n, dtype))
+
+
+def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
+    return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, stream or None)
 
 
 TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -182,6 +197,18 @@ def inv_(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=
                  _dtype_code(t, mixed), _stream_handle(stream))
     check(st, "tri_inv")
     return t
+
+
+def general_inv(a, mixed: bool = False, stream=None):
+    """Out of place A^-1 of a square CUDA tensor (float32 or float64) by the unpivoted
+    block LU of gen_inv.  Row-major A is column-major A^T, and (A^T)^-1 = (A^-1)^T, so the
+    column-major call on the row-major buffer returns A^-1 in row-major order."""
+    _rowmajor_square(a)
+    out = a.contiguous().clone()
+    n = out.shape[0]
+    st = gen_inv(n, out.data_ptr(), max(1, out.stride(0)), _dtype_code(out, mixed), _stream_handle(stream))
+    check(st, "gen_inv")
+    return out
 
 
 def inv(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=None):
