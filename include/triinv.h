@@ -122,6 +122,40 @@ TRI_API tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, 
                               size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Batched triangular inverses of uneven sizes, in place (block-Jacobi preconditioners):
+ * every block is inverted by the recursive split (Section 4.1, block count 2) with CRIT
+ * leaves (Section 4.2), entirely in shared memory, inside ONE persistent kernel whose
+ * CTAs take blocks from an atomic queue, largest first.
+ *   count  number of blocks (>= 0);  sizes: HOST array of count orders (0 <= n_i <= 256
+ *          for FP32, <= 128 for FP64, else TRI_ERR_UNSUPPORTED);  ptrs: HOST array of
+ *          count DEVICE pointers, block i column-major with leading dimension n_i.
+ *   uplo, diag apply to every block; dtype TRI_F32 (TRI_F32_MIXED is the same FP32
+ *   path: blocks of at most 256 are far below the size where split products pay) or
+ *   TRI_F64.
+ * Singular blocks: the smallest index i of a block with a zero or non-finite pivot is
+ * recorded and reported by tri_get_info (as the "index").
+ *
+ * tri_batched_plan_create uploads the descriptors (sorted by size), picks the thread
+ * count by timing the candidates on a scratch batch of the same sizes (the caller's data
+ * is not touched), and captures {queue reset, persistent kernel} in a CUDA graph.  It
+ * allocates device memory and synchronises; call it outside stream capture.
+ * tri_batched_exec replays the graph on `stream` (asynchronous; the blocks must not be
+ * in use by other work).  tri_batched_plan_destroy frees the plan (after the last
+ * tri_batched_exec that uses it has completed).
+ * tri_inv_batched = create + exec + synchronise `stream` + destroy.
+ * --------------------------------------------------------------------------------- */
+typedef struct tri_batched_plan tri_batched_plan;
+TRI_API tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *const *ptrs,
+                                           tri_uplo uplo, tri_diag diag, tri_dtype dtype,
+                                           tri_batched_plan **out);
+TRI_API tri_status tri_batched_exec(tri_batched_plan *plan, void *stream);
+TRI_API tri_status tri_batched_plan_destroy(tri_batched_plan *plan);
+/* Thread count the autotuner chose for this plan (diagnostic). */
+TRI_API int tri_batched_plan_threads(const tri_batched_plan *plan);
+TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs,
+                                   tri_uplo uplo, tri_diag diag, tri_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * tri_inv_noalloc -- tri_inv for callers that cannot allocate device memory.
  * The paper has no counterpart; this is an integration entry point.
  *

@@ -1,0 +1,498 @@
+// batched.cu -- a6: thousands of triangular blocks of uneven sizes in one persistent,
+// graph-captured launch (block-Jacobi preconditioner shape).
+//
+// Each CTA repeatedly takes the next block from an atomic queue (blocks sorted by size,
+// largest first, so the tail is made of small blocks), and inverts it entirely in shared
+// memory by the recursive triangular split of the paper:
+//   * the lower triangle is stored as 32 x 32 tiles (tile (I, J), I >= J, at index
+//     I(I+1)/2 + J; row pitch 33 keeps warp accesses conflict-free);
+//   * each diagonal tile is inverted by one warp with the CRIT column recurrence
+//     (Section 4.2): lane j holds column j of the inverse in registers;
+//   * split levels h = 32, 64, 128: for every pair, W = B X_A then B <- -X_C W (block
+//     inverse of the proof of the main Theorem, Section 3), as 32 x 32 x 32 warp tile
+//     products (each lane a 4 x 8 register block).
+// Blocks larger than the shared-memory budget are rejected at plan time
+// (TRI_ERR_UNSUPPORTED): 256 in FP32, 128 in FP64.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct tri_batched_plan;   // opaque to callers (include/triinv.h)
+
+namespace triinv {
+namespace {
+
+constexpr int TP = 33;   // tile row pitch (elements)
+constexpr int TE = 32 * TP;
+
+struct BDesc {
+    void *ptr;
+    long long ld;
+    int n;
+    int index;   // position in the caller's arrays
+};
+
+template <int MAXT>
+struct BLimits {
+    static constexpr int kTiles = MAXT * (MAXT + 1) / 2;   // lower tiles of the largest block
+    static constexpr int kWTiles = (MAXT / 2) * (MAXT / 2); // W of the top level
+};
+
+template <typename T>
+__device__ __forceinline__ T *tile_ptr(T *tiles, int I, int J) {
+    return tiles + (size_t)(I * (I + 1) / 2 + J) * TE;
+}
+
+// Warp tile product: acc[4][8] += A (32x32) * B (32x32), lane = (row group, col group).
+template <typename T>
+__device__ __forceinline__ void warp_mma32(const T *A, const T *B, T (&acc)[4][8], int lane) {
+    const int r0 = (lane >> 2) * 4, c0 = (lane & 3) * 8;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        T a[4], b[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[(r0 + i) * TP + k];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = B[k * TP + c0 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_store32(T *C, const T (&acc)[4][8], int lane, T scale) {
+    const int r0 = (lane >> 2) * 4, c0 = (lane & 3) * 8;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) C[(r0 + i) * TP + c0 + j] = scale * acc[i][j];
+}
+
+// In-place inverse of a lower 32 x 32 tile by one warp (column recurrence; lane j owns
+// column j).  Returns true if a pivot among the first `valid` rows is zero or non-finite.
+template <typename T>
+__device__ __forceinline__ bool warp_tile_inverse(T *t, int lane, int valid) {
+    T x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const T tkk = t[k * TP + k];
+        if (k < valid && (tkk == T(0) || !isfinite(tkk))) bad = true;
+        const T dk = T(1) / tkk;
+        // row k of the inverse becomes final
+        if (lane == k) x[k] = dk;
+        else if (lane < k) x[k] = -x[k] * dk;
+        // pending rows: x_ij += t_ik x_kj  (lanes j > k hold x_kj = 0)
+#pragma unroll
+        for (int i = k + 1; i < 32; ++i) x[i] = fma(t[i * TP + k], x[k], x[i]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) t[i * TP + lane] = (i >= lane) ? x[i] : T(0);
+    __syncwarp();
+    return bad;
+}
+
+template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
+__global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict__ descs, int count, int *counter, long long *info) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    T *tiles = reinterpret_cast<T *>(smem_raw);
+    T *wt = tiles + (size_t)BLimits<MAXT>::kTiles * TE;
+    __shared__ int s_job;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+
+    for (;;) {
+        if (tid == 0) s_job = atomicAdd(counter, 1);
+        __syncthreads();
+        const int job = s_job;
+        __syncthreads();
+        if (job >= count) break;
+        const BDesc d = descs[job];
+        const int n = d.n, nt = (n + 31) / 32;
+        const T *g = reinterpret_cast<const T *>(d.ptr);
+        const long long ld = d.ld;
+
+        // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
+        // One warp per tile, 32 independent loads in flight per lane.
+        const int ntl = nt * (nt + 1) / 2;
+        for (int tl = warp; tl < ntl; tl += nwarps) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+            const int J = tl - I * (I + 1) / 2;
+            T v[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                // lane = row (column-major source) or column (transposed source)
+                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+                const int gi = I * 32 + r, gj = J * 32 + c;
+                if (gi < n && gj < n) {
+                    if (gj < gi) v[q] = g[vidx<TRANS>(gi, gj, ld)];
+                    else if (gj == gi) v[q] = UNIT ? T(1) : g[vidx<TRANS>(gi, gi, ld)];
+                    else v[q] = T(0);
+                } else {
+                    v[q] = (gi == gj) ? T(1) : T(0);
+                }
+            }
+            T *tp = tile_ptr(tiles, I, J);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+                tp[r * TP + c] = v[q];
+            }
+        }
+        __syncthreads();
+
+        // Diagonal tiles.
+        for (int I = warp; I < nt; I += nwarps) {
+            const bool bad = warp_tile_inverse(tile_ptr(tiles, I, I), lane, min(32, n - I * 32));
+            if (bad && lane == 0 && !UNIT) atomicMin(info, (long long)d.index);
+        }
+        __syncthreads();
+
+        // Split levels (in tiles): ht = 1, 2, 4.
+        for (int ht = 1; ht < nt; ht *= 2) {
+            const int pairs = (nt - ht + 2 * ht - 1) / (2 * ht);
+            // W_q(Iw, Jw) = sum_{K >= Jw} B(c0 + Iw, a0 + K) X(a0 + K, a0 + Jw)
+            int jobs = 0;
+            for (int q = 0; q < pairs; ++q) jobs += min(ht, nt - (2 * q * ht + ht)) * ht;
+            for (int jb = warp; jb < jobs; jb += nwarps) {
+                int q = 0, rest = jb;
+                for (;;) {
+                    const int hc = min(ht, nt - (2 * q * ht + ht));
+                    if (rest < hc * ht) break;
+                    rest -= hc * ht;
+                    ++q;
+                }
+                const int a0 = 2 * q * ht, c0 = a0 + ht;
+                const int Iw = rest / ht, Jw = rest % ht;
+                T acc[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+                for (int K = Jw; K < ht; ++K)
+                    warp_mma32(tile_ptr(tiles, c0 + Iw, a0 + K), tile_ptr(tiles, a0 + K, a0 + Jw), acc, lane);
+                warp_store32(wt + (size_t)jb * TE, acc, lane, T(1));
+            }
+            __syncthreads();
+            // B(c0 + Iw, a0 + Jw) <- -sum_{K <= Iw} X_C(c0 + Iw, c0 + K) W_q(K, Jw)
+            for (int jb = warp; jb < jobs; jb += nwarps) {
+                int q = 0, rest = jb, base = 0;
+                for (;;) {
+                    const int hc = min(ht, nt - (2 * q * ht + ht));
+                    if (rest < hc * ht) break;
+                    rest -= hc * ht;
+                    base += hc * ht;
+                    ++q;
+                }
+                const int a0 = 2 * q * ht, c0 = a0 + ht;
+                const int Iw = rest / ht, Jw = rest % ht;
+                T acc[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+                for (int K = 0; K <= Iw; ++K)
+                    warp_mma32(tile_ptr(tiles, c0 + Iw, c0 + K), wt + (size_t)(base + K * ht + Jw) * TE, acc, lane);
+                warp_store32(tile_ptr(tiles, c0 + Iw, a0 + Jw), acc, lane, T(-1));
+            }
+            __syncthreads();
+        }
+
+        // Store the lower triangle back (unit diagonal not written), one warp per tile.
+        T *go = reinterpret_cast<T *>(d.ptr);
+        for (int tl = warp; tl < ntl; tl += nwarps) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+            const int J = tl - I * (I + 1) / 2;
+            const T *tp = tile_ptr(tiles, I, J);
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+                const int gi = I * 32 + r, gj = J * 32 + c;
+                if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = tp[r * TP + c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int MAXT>
+size_t smem_bytes() {
+    return (size_t)(BLimits<MAXT>::kTiles + BLimits<MAXT>::kWTiles) * TE * sizeof(T);
+}
+
+using KernFn = void (*)(const BDesc *, int, int *, long long *);
+
+template <typename T, int MAXT, int NT>
+KernFn pick3(bool trans, bool unit) {
+    if (trans) return unit ? batched_kernel<T, true, true, MAXT, NT> : batched_kernel<T, true, false, MAXT, NT>;
+    return unit ? batched_kernel<T, false, true, MAXT, NT> : batched_kernel<T, false, false, MAXT, NT>;
+}
+
+// Kernel for a precision, orientation, diagonal kind and thread count (256 or 512).
+KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *smem) {
+    if (dt == TRI_F64) {
+        *smem = smem_bytes<double, 4>();
+        return threads == 256 ? pick3<double, 4, 256>(trans, unit) : pick3<double, 4, 512>(trans, unit);
+    }
+    *smem = smem_bytes<float, 8>();
+    return threads == 256 ? pick3<float, 8, 256>(trans, unit) : pick3<float, 8, 512>(trans, unit);
+}
+
+}  // namespace
+}  // namespace triinv
+
+struct tri_batched_plan {
+    int device = 0;
+    int count = 0;
+    tri_dtype dtype = TRI_F32;
+    bool trans = false, unit = false;
+    triinv::BDesc *d_desc = nullptr;   // sorted, largest first
+    int *d_counter = nullptr;
+    int threads = 512;
+    int ctas = 0;
+    size_t smem = 0;
+    double flops = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace triinv {
+namespace {
+
+int max_block(tri_dtype dt) { return dt == TRI_F64 ? 128 : 256; }
+
+// Dynamic shared memory above 48 KB must be allowed per kernel before any launch (and
+// before stream capture).
+cudaError_t allow_smem(tri_dtype dt, bool trans) {
+    for (int u = 0; u < 2; ++u)
+        for (int th : {256, 512}) {
+            size_t smem = 0;
+            KernFn k = pick_kernel(dt, trans, u != 0, th, &smem);
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+cudaError_t launch_plan_kernel(const tri_batched_plan *p, cudaStream_t s, long long *info, int threads) {
+    size_t smem = 0;
+    KernFn k = pick_kernel(p->dtype, p->trans, p->unit, threads, &smem);
+    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k<<<p->ctas, threads, smem, s>>>(p->d_desc, p->count, p->d_counter, info);
+    return cudaGetLastError();
+}
+
+// Autotuner: time each candidate thread count on a scratch copy of the batch shape
+// (identity blocks of the same sizes, so the caller's data is untouched) and keep the
+// fastest.  Results are cached per (device, size histogram) for the process.
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, int>> g_tune_cache;
+
+int autotune(tri_batched_plan *p, const std::vector<int64_t> &sizes_sorted, const Ctx &c) {
+    std::string key = std::to_string(c.device) + ":" + std::to_string((int)p->dtype) + ":";
+    {
+        // histogram of sizes in 16-wide buckets
+        std::vector<int> h(33, 0);
+        for (int64_t s : sizes_sorted) h[std::min<int64_t>(32, s / 16)]++;
+        for (int v : h) key += std::to_string(v) + ",";
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) return kv.second;
+    }
+    const char *env = getenv("TRI_BATCHED_THREADS");
+    if (env) return atoi(env) == 256 ? 256 : 512;
+    // scratch blocks (identity), same sizes, dense column-major
+    size_t total = 0;
+    for (int64_t s : sizes_sorted) total += (size_t)s * s;
+    const size_t es = p->dtype == TRI_F64 ? 8 : 4;
+    void *scratch = nullptr;
+    BDesc *d_scr = nullptr;
+    long long *d_info = nullptr;
+    int best = 512;
+    if (cudaMalloc(&scratch, total * es) != cudaSuccess || cudaMalloc(&d_scr, sizeof(BDesc) * sizes_sorted.size()) != cudaSuccess ||
+        cudaMalloc(&d_info, sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(scratch);
+        cudaFree(d_scr);
+        cudaFree(d_info);
+        return best;
+    }
+    cudaMemset(scratch, 0, total * es);
+    std::vector<BDesc> hd(sizes_sorted.size());
+    size_t off = 0;
+    for (size_t i = 0; i < sizes_sorted.size(); ++i) {
+        hd[i] = BDesc{(uint8_t *)scratch + off * es, (long long)sizes_sorted[i], (int)sizes_sorted[i], (int)i};
+        off += (size_t)sizes_sorted[i] * sizes_sorted[i];
+    }
+    cudaMemcpy(d_scr, hd.data(), sizeof(BDesc) * hd.size(), cudaMemcpyHostToDevice);
+    tri_batched_plan tmp = *p;
+    tmp.d_desc = d_scr;
+    tmp.unit = true;   // identity scratch: unit diagonal, no pivots to check
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int th : {256, 512}) {
+        float ms = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, c.stream);
+            ok = launch_plan_kernel(&tmp, c.stream, d_info, th) == cudaSuccess;
+            cudaEventRecord(e1, c.stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;
+        }
+        if (ok && ms < best_ms) {
+            best_ms = ms;
+            best = th;
+        }
+        cudaGetLastError();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    cudaFree(d_scr);
+    cudaFree(d_info);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.push_back({key, best});
+    return best;
+}
+
+}  // namespace
+}  // namespace triinv
+
+using namespace triinv;
+
+extern "C" {
+
+tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *const *ptrs, tri_uplo uplo,
+                                   tri_diag diag, tri_dtype dtype, tri_batched_plan **out) {
+    if (!out || count < 0 || (count > 0 && (!sizes || !ptrs))) return TRI_ERR_ARG;
+    if ((uplo != TRI_LOWER && uplo != TRI_UPPER) || (diag != TRI_NONUNIT && diag != TRI_UNIT)) return TRI_ERR_ARG;
+    if (dtype != TRI_F64 && dtype != TRI_F32 && dtype != TRI_F32_MIXED) return TRI_ERR_ARG;
+    if (count > INT_MAX / 2) return TRI_ERR_ARG;
+    *out = nullptr;
+    const tri_dtype dt = dtype == TRI_F64 ? TRI_F64 : TRI_F32;
+    for (int64_t i = 0; i < count; ++i) {
+        if (sizes[i] < 0 || (sizes[i] > 0 && !ptrs[i])) return TRI_ERR_ARG;
+        if (sizes[i] > max_block(dt)) return TRI_ERR_UNSUPPORTED;
+    }
+    Ctx c;
+    tri_status st = device_ctx_public(nullptr, &c);
+    if (st != TRI_OK) return st;
+    tri_batched_plan *p = new tri_batched_plan();
+    p->device = c.device;
+    p->dtype = dt;
+    p->trans = uplo == TRI_UPPER;
+    p->unit = diag == TRI_UNIT;
+    std::vector<int64_t> order;
+    for (int64_t i = 0; i < count; ++i)
+        if (sizes[i] > 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return sizes[a] > sizes[b]; });
+    std::vector<BDesc> hd;
+    std::vector<int64_t> ss;
+    for (int64_t i : order) {
+        hd.push_back(BDesc{ptrs[i], (long long)sizes[i], (int)sizes[i], (int)i});
+        ss.push_back(sizes[i]);
+        p->flops += (double)sizes[i] * sizes[i] * sizes[i] / 3.0;
+    }
+    p->count = (int)hd.size();
+    if (cudaMalloc(&p->d_counter, sizeof(int)) != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    if (p->count > 0) {
+        if (cudaMalloc(&p->d_desc, sizeof(BDesc) * hd.size()) != cudaSuccess) {
+            cudaFree(p->d_counter);
+            delete p;
+            cudaGetLastError();
+            return TRI_ERR_NOMEM;
+        }
+        cudaMemcpy(p->d_desc, hd.data(), sizeof(BDesc) * hd.size(), cudaMemcpyHostToDevice);
+    }
+    pick_kernel(p->dtype, p->trans, p->unit, 512, &p->smem);
+    if (allow_smem(p->dtype, p->trans) != cudaSuccess) {
+        cudaGetLastError();
+        tri_batched_plan_destroy(p);
+        return TRI_ERR_CUDA;
+    }
+    p->ctas = std::max(1, std::min(c.sm_count, p->count));
+    p->threads = p->count > 0 ? autotune(p, ss, c) : 512;
+    // Capture {reset queue, persistent kernel} once; tri_batched_exec replays it.
+    if (p->count > 0) {
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            tri_batched_plan_destroy(p);
+            return TRI_ERR_CUDA;
+        }
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        ok = ok && launch_plan_kernel(p, cs, c.info, p->threads) == cudaSuccess;
+        ok = (cudaStreamEndCapture(cs, &p->graph) == cudaSuccess) && ok;
+        ok = ok && cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
+        cudaStreamDestroy(cs);
+        if (!ok) {
+            cudaGetLastError();
+            tri_batched_plan_destroy(p);
+            return TRI_ERR_CUDA;
+        }
+    }
+    *out = p;
+    return TRI_OK;
+}
+
+tri_status tri_batched_exec(tri_batched_plan *plan, void *stream) {
+    if (!plan) return TRI_ERR_ARG;
+    if (plan->count == 0) return TRI_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return TRI_ERR_ARG;
+    TraceScope ts((cudaStream_t)stream, plan->dtype == TRI_F64 ? "batched_f64" : "batched_f32", plan->flops, 0.0);
+    return cudaGraphLaunch(plan->exec, (cudaStream_t)stream) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+tri_status tri_batched_plan_destroy(tri_batched_plan *plan) {
+    if (!plan) return TRI_OK;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    cudaFree(plan->d_desc);
+    cudaFree(plan->d_counter);
+    delete plan;
+    return TRI_OK;
+}
+
+int tri_batched_plan_threads(const tri_batched_plan *plan) { return plan ? plan->threads : 0; }
+
+tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs, tri_uplo uplo, tri_diag diag,
+                           tri_dtype dtype, void *stream) {
+    tri_batched_plan *p = nullptr;
+    tri_status st = tri_batched_plan_create(count, sizes, ptrs, uplo, diag, dtype, &p);
+    if (st != TRI_OK) return st;
+    st = tri_batched_exec(p, stream);
+    // The plan's buffers may still be in use by the queued launch.
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess && st == TRI_OK) st = TRI_ERR_CUDA;
+    tri_batched_plan_destroy(p);
+    return st;
+}
+
+}  // extern "C"

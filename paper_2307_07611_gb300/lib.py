@@ -46,6 +46,12 @@ def _declare(lib):
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "gen_inv": ([i64, vp, i64, i32, vp], i32),
+        "tri_batched_plan_create": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32,
+                                     ctypes.POINTER(vp)], i32),
+        "tri_batched_exec": ([vp, vp], i32),
+        "tri_batched_plan_destroy": ([vp], i32),
+        "tri_batched_plan_threads": ([vp], i32),
+        "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
         "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
@@ -110,6 +116,36 @@ def gen_inv_workspace_size(n, dtype) -> int:
 
 def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
     return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, stream or None)
+
+
+def _arrays(sizes, ptrs):
+    n = len(sizes)
+    return (ctypes.c_int64 * n)(*[int(x) for x in sizes]), (ctypes.c_void_p * n)(*[int(p) for p in ptrs])
+
+
+def tri_batched_plan_create(count, sizes, ptrs, uplo, diag, dtype):
+    """Returns (status, plan handle)."""
+    sz, pt = _arrays(sizes, ptrs)
+    h = ctypes.c_void_p()
+    st = load().tri_batched_plan_create(count, sz, pt, uplo, diag, dtype, ctypes.byref(h))
+    return st, h
+
+
+def tri_batched_exec(plan, stream=0) -> int:
+    return load().tri_batched_exec(plan, stream or None)
+
+
+def tri_batched_plan_destroy(plan) -> int:
+    return load().tri_batched_plan_destroy(plan)
+
+
+def tri_batched_plan_threads(plan) -> int:
+    return load().tri_batched_plan_threads(plan)
+
+
+def tri_inv_batched(count, sizes, ptrs, uplo, diag, dtype, stream=0) -> int:
+    sz, pt = _arrays(sizes, ptrs)
+    return load().tri_inv_batched(count, sz, pt, uplo, diag, dtype, stream or None)
 
 
 TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
