@@ -156,6 +156,45 @@ TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *co
                                    tri_uplo uplo, tri_diag diag, tri_dtype dtype, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Strided batch of equal-order triangular inverses, in place: matrix b starts at
+ * a + b * stride (elements, stride >= lda * n).  TRI_F32 / TRI_F64 run every split level
+ * of all matrices in one launch (batch <= 65535); TRI_F32_MIXED inverts them one after
+ * another with the mixed path.  Singular pivots record the matrix index.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                                           int64_t stride, int64_t batch, tri_dtype dtype, void *stream);
+TRI_API size_t tri_inv_strided_batched_workspace_size(int64_t n, int64_t batch, tri_dtype dtype);
+TRI_API tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                                              int64_t stride, int64_t batch, tri_dtype dtype, void *workspace,
+                                              size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Adjoint of X = T^-1 (not in the paper; the plain definition from
+ * d(T^-1) = -T^-1 dT T^-1): given X (the forward result, `uplo` triangle, unit diagonal
+ * implied for TRI_UNIT) and the cotangent G = dL/dX (full n x n, only the `uplo`
+ * triangle of G contributes), writes
+ *     dT = -P(X^T G X^T)
+ * into the `uplo` triangle of dt (the diagonal is set to 0 for TRI_UNIT); the other
+ * triangle of dt is not written.  All matrices column-major, device memory; x, g and dt
+ * must not overlap.  TRI_F32 / TRI_F64: CUDA-core products; TRI_F32_MIXED: split-BF16
+ * tensor-core products (three terms) for n >= 256.  Scratch: n*n elements per matrix
+ * (plus BF16 planes for TRI_F32_MIXED), from the stream-ordered allocator or `_ex`.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_inv_backward(tri_uplo uplo, tri_diag diag, int64_t n, const void *x, int64_t ldx,
+                                    const void *g, int64_t ldg, void *dt, int64_t lddt, tri_dtype dtype,
+                                    void *stream);
+TRI_API tri_status tri_inv_backward_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, const void *x,
+                                                    int64_t ldx, int64_t stride_x, const void *g, int64_t ldg,
+                                                    int64_t stride_g, void *dt, int64_t lddt, int64_t stride_dt,
+                                                    int64_t batch, tri_dtype dtype, void *stream);
+TRI_API size_t tri_inv_backward_workspace_size(int64_t n, int64_t batch, tri_dtype dtype);
+TRI_API tri_status tri_inv_backward_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, const void *x,
+                                                       int64_t ldx, int64_t stride_x, const void *g, int64_t ldg,
+                                                       int64_t stride_g, void *dt, int64_t lddt, int64_t stride_dt,
+                                                       int64_t batch, tri_dtype dtype, void *workspace,
+                                                       size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * tri_inv_noalloc -- tri_inv for callers that cannot allocate device memory.
  * The paper has no counterpart; this is an integration entry point.
  *

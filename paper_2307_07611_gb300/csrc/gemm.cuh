@@ -26,7 +26,11 @@ struct GemmArgs {
     double beta;
     void *c;
     int64_t ldc;
-    int cmask;   // OP_FULL, OP_LOWER or OP_UPPER: which part of C is written
+    int cmask;   // OP_FULL, OP_LOWER or OP_UPPER: which part of C is written;
+                 // OP_LOWER_UNIT / OP_UPPER_UNIT: the strict triangle, diagonal set to 0
+    bool ta = false, tb = false;              // use A^T / B^T (stored column-major)
+    int64_t batch = 1;                        // independent products, pointers advanced by
+    int64_t sa = 0, sb = 0, sc = 0;           // these strides (elements)
 };
 
 double gemm_flops(const GemmArgs &g);

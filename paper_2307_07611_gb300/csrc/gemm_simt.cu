@@ -25,24 +25,26 @@ __device__ __forceinline__ int gmicro(int t, int r) {
     return t * TX + r;
 }
 
-// Element (r, c) of a triangular-kind operand; rows/cols are the operand's own indices.
+// Element (r, c) of op(P) (P or P^T, P column-major) for a triangular-kind operand;
+// r, c index op(P).  Entries outside the triangle are never read.
 template <typename T>
-__device__ __forceinline__ T tri_fetch(const T *p, int64_t ld, int kind, int64_t r, int64_t c) {
+__device__ __forceinline__ T tri_fetch(const T *p, int64_t ld, bool tr, int kind, int64_t r, int64_t c) {
+    const int64_t o = tr ? (c + r * ld) : (r + c * ld);
     switch (kind) {
-        case OP_FULL: return p[r + c * ld];
-        case OP_LOWER: return c <= r ? p[r + c * ld] : T(0);
-        case OP_UPPER: return c >= r ? p[r + c * ld] : T(0);
-        case OP_LOWER_UNIT: return c < r ? p[r + c * ld] : (c == r ? T(1) : T(0));
-        case OP_UPPER_UNIT: return c > r ? p[r + c * ld] : (c == r ? T(1) : T(0));
+        case OP_FULL: return p[o];
+        case OP_LOWER: return c <= r ? p[o] : T(0);
+        case OP_UPPER: return c >= r ? p[o] : T(0);
+        case OP_LOWER_UNIT: return c < r ? p[o] : (c == r ? T(1) : T(0));
+        case OP_UPPER_UNIT: return c > r ? p[o] : (c == r ? T(1) : T(0));
     }
     return T(0);
 }
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
 __global__ void __launch_bounds__(GCfg<T, BM, BN, BK, TM, TN>::NT)
 gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__ A, int64_t lda,
                  int akind, const T *__restrict__ B, int64_t ldb, int bkind, T beta, T *C,
-                 int64_t ldc, int cmask) {
+                 int64_t ldc, int cmask, int64_t sa, int64_t sb, int64_t sc) {
     using Cf = GCfg<T, BM, BN, BK, TM, TN>;
     constexpr int NT = Cf::NT;
     __shared__ __align__(16) T As[2][BK][BM + Cf::PAD];
@@ -51,9 +53,14 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     const int64_t m0 = (int64_t)blockIdx.y * BM;
     const int64_t n0 = (int64_t)blockIdx.x * BN;
     if (m0 >= M || n0 >= N) return;
+    A += (int64_t)blockIdx.z * sa;
+    B += (int64_t)blockIdx.z * sb;
+    C += (int64_t)blockIdx.z * sc;
     // Output mask: skip tiles entirely outside the stored triangle.
-    if (cmask == OP_LOWER && n0 > m0 + BM - 1) return;
-    if (cmask == OP_UPPER && m0 > n0 + BN - 1) return;
+    const bool c_low = cmask == OP_LOWER || cmask == OP_LOWER_UNIT;
+    const bool c_up = cmask == OP_UPPER || cmask == OP_UPPER_UNIT;
+    if (c_low && n0 > m0 + BM - 1) return;
+    if (c_up && m0 > n0 + BN - 1) return;
 
     int64_t kbeg = 0, kend = K;
     const bool a_low = (akind == OP_LOWER || akind == OP_LOWER_UNIT);
@@ -66,32 +73,43 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     if (b_up) kend = min(kend, n0 + BN);           // B(k,n) = 0 for k > n
 
     T ra[Cf::A_PER], rb[Cf::B_PER];
+    // Thread -> element maps follow the contiguous index of each operand in memory.
+    auto amap = [&](int idx, int &m, int &k) {
+        if (TA) { k = idx % BK; m = idx / BK; }
+        else { m = idx % BM; k = idx / BM; }
+    };
+    auto bmap = [&](int idx, int &k, int &nn) {
+        if (TB) { nn = idx % BN; k = idx / BN; }
+        else { k = idx % BK; nn = idx / BK; }
+    };
     auto gload = [&](int64_t kt) {
 #pragma unroll
         for (int r = 0; r < Cf::A_PER; ++r) {
-            const int idx = tid + r * NT;
-            const int m = idx % BM, k = idx / BM;
+            int m, k;
+            amap(tid + r * NT, m, k);
             const int64_t gm = m0 + m, gk = kt + k;
-            ra[r] = (gm < M && gk < kend) ? tri_fetch(A, lda, akind, gm, gk) : T(0);
+            ra[r] = (gm < M && gk < kend) ? tri_fetch(A, lda, TA, akind, gm, gk) : T(0);
         }
 #pragma unroll
         for (int r = 0; r < Cf::B_PER; ++r) {
-            const int idx = tid + r * NT;
-            const int k = idx % BK, nn = idx / BK;
+            int k, nn;
+            bmap(tid + r * NT, k, nn);
             const int64_t gk = kt + k, gn = n0 + nn;
-            rb[r] = (gn < N && gk < kend) ? tri_fetch(B, ldb, bkind, gk, gn) : T(0);
+            rb[r] = (gn < N && gk < kend) ? tri_fetch(B, ldb, TB, bkind, gk, gn) : T(0);
         }
     };
     auto sstore = [&](int buf) {
 #pragma unroll
         for (int r = 0; r < Cf::A_PER; ++r) {
-            const int idx = tid + r * NT;
-            As[buf][idx / BM][idx % BM] = ra[r];
+            int m, k;
+            amap(tid + r * NT, m, k);
+            As[buf][k][m] = ra[r];
         }
 #pragma unroll
         for (int r = 0; r < Cf::B_PER; ++r) {
-            const int idx = tid + r * NT;
-            Bs[buf][idx % BK][idx / BK] = rb[r];
+            int k, nn;
+            bmap(tid + r * NT, k, nn);
+            Bs[buf][k][nn] = rb[r];
         }
     };
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
@@ -135,22 +153,34 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
         for (int j = 0; j < TN; ++j) {
             const int64_t gn = n0 + gmicro<BN, TN>(tx, j);
             if (gn >= N) continue;
-            if (cmask == OP_LOWER && gn > gm) continue;
-            if (cmask == OP_UPPER && gm > gn) continue;
+            if (c_low && gn > gm) continue;
+            if (c_up && gm > gn) continue;
             T *c = C + gm + gn * ldc;
+            if ((cmask == OP_LOWER_UNIT || cmask == OP_UPPER_UNIT) && gm == gn) {
+                *c = T(0);
+                continue;
+            }
             *c = beta == T(0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
         }
     }
 }
 
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
+cudaError_t launch_g2(const Ctx &c, const GemmArgs &g) {
+    using Cf = GCfg<T, BM, BN, BK, TM, TN>;
+    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM), (unsigned)g.batch);
+    gemm_simt_kernel<T, BM, BN, BK, TM, TN, TA, TB><<<grid, Cf::NT, 0, c.stream>>>(
+        g.m, g.n, g.k, (T)g.alpha, (const T *)g.a, g.lda, g.akind, (const T *)g.b, g.ldb, g.bkind,
+        (T)g.beta, (T *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc);
+    return cudaGetLastError();
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_g(const Ctx &c, const GemmArgs &g) {
-    using Cf = GCfg<T, BM, BN, BK, TM, TN>;
-    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM));
-    gemm_simt_kernel<T, BM, BN, BK, TM, TN><<<grid, Cf::NT, 0, c.stream>>>(
-        g.m, g.n, g.k, (T)g.alpha, (const T *)g.a, g.lda, g.akind, (const T *)g.b, g.ldb, g.bkind,
-        (T)g.beta, (T *)g.c, g.ldc, g.cmask);
-    return cudaGetLastError();
+    if (g.ta) return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, true, true>(c, g)
+                          : launch_g2<T, BM, BN, BK, TM, TN, true, false>(c, g);
+    return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, false, true>(c, g)
+                : launch_g2<T, BM, BN, BK, TM, TN, false, false>(c, g);
 }
 
 }  // namespace
@@ -169,8 +199,9 @@ double gemm_flops(const GemmArgs &g) {
 }
 
 cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name) {
-    if (g.m <= 0 || g.n <= 0) return cudaSuccess;
-    TraceScope ts(c.stream, trace_name, gemm_flops(g), 0.0);
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return cudaSuccess;
+    if (g.batch > 65535) return cudaErrorInvalidValue;
+    TraceScope ts(c.stream, trace_name, gemm_flops(g) * (double)g.batch, 0.0);
     if (dt == TRI_F64) return launch_g<double, 64, 64, 16, 4, 4>(c, g);
     if (g.m >= 128 && g.n >= 128) return launch_g<float, 128, 128, 8, 8, 8>(c, g);
     return launch_g<float, 64, 64, 16, 4, 4>(c, g);

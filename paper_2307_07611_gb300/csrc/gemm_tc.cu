@@ -17,7 +17,7 @@ namespace triinv {
 
 cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t rows, int64_t cols,
                               int kind, __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
-                              int64_t ldp);
+                              int64_t ldp, bool trans);
 
 namespace {
 
@@ -47,8 +47,8 @@ cudaError_t tile_list(const Ctx &c, const GemmArgs &g, int terms, TileList *out)
     std::vector<tc::Tile> v;
     for (int64_t m0 = 0; m0 < g.m; m0 += tc::BM) {
         for (int64_t n0 = 0; n0 < g.n; n0 += tc::BN) {
-            if (g.cmask == OP_LOWER && n0 > m0 + tc::BM - 1) continue;
-            if (g.cmask == OP_UPPER && m0 > n0 + tc::BN - 1) continue;
+            if ((g.cmask == OP_LOWER || g.cmask == OP_LOWER_UNIT) && n0 > m0 + tc::BM - 1) continue;
+            if ((g.cmask == OP_UPPER || g.cmask == OP_UPPER_UNIT) && m0 > n0 + tc::BN - 1) continue;
             int64_t kbeg = 0, kend = g.k;
             if (is_low(g.akind)) kend = std::min(kend, m0 + tc::BM);
             if (is_up(g.akind)) kbeg = std::max(kbeg, m0);
@@ -81,6 +81,19 @@ size_t gemm_tc_ws_bytes(int64_t m, int64_t n, int64_t k) {
 
 cudaError_t gemm_tc(const Ctx &c, const GemmArgs &g, int terms, void *ws, const char *trace_name) {
     if (g.m <= 0 || g.n <= 0) return cudaSuccess;
+    if (g.batch > 1) {
+        // One product per batch element (the planes of one element at a time).
+        GemmArgs one = g;
+        one.batch = 1;
+        for (int64_t b = 0; b < g.batch; ++b) {
+            one.a = (const uint8_t *)g.a + b * g.sa * 4;
+            one.b = (const uint8_t *)g.b + b * g.sb * 4;
+            one.c = (uint8_t *)g.c + b * g.sc * 4;
+            cudaError_t e = gemm_tc(c, one, terms, ws, trace_name);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (terms != 1 && terms != 3 && terms != 6) return cudaErrorInvalidValue;
     const int64_t lda = rup(g.m, 64), ldb = rup(g.k, 64);
     uint8_t *base = (uint8_t *)ws;
@@ -92,10 +105,10 @@ cudaError_t gemm_tc(const Ctx &c, const GemmArgs &g, int terms, void *ws, const 
     }
     const bool three = terms == 6;
     cudaError_t e = launch_split_rect(c, (const float *)g.a, g.lda, g.m, g.k, g.akind, A[0], A[1],
-                                      three ? A[2] : nullptr, lda);
+                                      three ? A[2] : nullptr, lda, g.ta);
     if (e != cudaSuccess) return e;
     e = launch_split_rect(c, (const float *)g.b, g.ldb, g.k, g.n, g.bkind, B[0], B[1],
-                          three ? B[2] : nullptr, ldb);
+                          three ? B[2] : nullptr, ldb, g.tb);
     if (e != cudaSuccess) return e;
     TileList tl;
     e = tile_list(c, g, terms, &tl);

@@ -43,8 +43,10 @@ struct TraceScope {
 // ---- leaf inverse (leaf.cu) -------------------------------------------------------
 // Inverts every diagonal block [q*leaf, min(q*leaf+leaf, n)) of the lower view in place
 // by the column recurrence.  leaf must be 16, 32 or 64.
+// batch > 1: `batch` matrices `bstride` elements apart (grid.y); singular pivots then
+// record the matrix index instead of the row.
 cudaError_t launch_leaf(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n,
-                        void *a, int64_t lda, int leaf);
+                        void *a, int64_t lda, int leaf, int64_t batch = 1, int64_t bstride = 0);
 
 // ---- SIMT level products (trmm_simt.cu) -------------------------------------------
 // One split level with half-size h: for every active pair q (A-block at q*2h, C-block
@@ -52,8 +54,10 @@ cudaError_t launch_leaf(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64
 //   mode 0:  W_q = B_q * X_A        (B_q: rows of C x cols of A; X_A lower)
 //   mode 1:  B_q <- -X_C * W_q      (X_C lower)
 // W is column-major with leading dimension h, pair q at offset q*h*h.
+// batch > 1: matrices `bstride` elements apart; W of matrix b at b * pairs * h * h.
 cudaError_t launch_trmm_level(const Ctx &c, tri_dtype dt, bool trans, bool unit, int mode,
-                              int64_t n, void *a, int64_t lda, int64_t h, void *w);
+                              int64_t n, void *a, int64_t lda, int64_t h, void *w,
+                              int64_t batch = 1, int64_t bstride = 0);
 
 // Number of active pairs at split half-size h.
 inline int64_t level_pairs(int64_t n, int64_t h) {

@@ -23,7 +23,7 @@ namespace {
 
 template <typename T, int LEAF, int NT, bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(NT) leaf_kernel(T *__restrict__ a, int64_t lda, int64_t n,
-                                                  long long *__restrict__ info) {
+                                                  long long *__restrict__ info, int64_t bstride) {
     static_assert(NT % LEAF == 0 && (LEAF * LEAF) % NT == 0, "thread layout");
     constexpr int G = NT / LEAF;          // row groups
     constexpr int RPT = LEAF * LEAF / NT; // rows per thread
@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel(T *__restrict__ a, int64_t lda
 
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * LEAF;
+    a += (int64_t)blockIdx.y * bstride;          // matrix of a strided batch
     const int nb = (int)((n - r0) < (int64_t)LEAF ? (n - r0) : (int64_t)LEAF);
 
     // Load the lower triangle of the leaf (the strict upper part and the padding become
@@ -53,7 +54,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel(T *__restrict__ a, int64_t lda
     __syncthreads();
     if (tid < LEAF) {
         T d = ts[tid][tid];
-        if (tid < nb && (d == T(0) || !isfinite(d))) atomicMin(info, (long long)(r0 + tid));
+        if (tid < nb && (d == T(0) || !isfinite(d)))
+            atomicMin(info, gridDim.y > 1 ? (long long)blockIdx.y : (long long)(r0 + tid));
         dinv[tid] = T(1) / d;
     }
     __syncthreads();
@@ -101,28 +103,29 @@ __global__ void __launch_bounds__(NT) leaf_kernel(T *__restrict__ a, int64_t lda
 }
 
 template <typename T, int LEAF>
-cudaError_t launch_leaf_t(const Ctx &c, bool trans, bool unit, int64_t n, T *a, int64_t lda) {
+cudaError_t launch_leaf_t(const Ctx &c, bool trans, bool unit, int64_t n, T *a, int64_t lda,
+                          int64_t batch, int64_t bstride) {
     constexpr int NT = LEAF >= 32 ? 256 : 128;
     const int64_t blocks = (n + LEAF - 1) / LEAF;
-    if (blocks <= 0) return cudaSuccess;
-    dim3 grid((unsigned)blocks);
+    if (blocks <= 0 || batch <= 0) return cudaSuccess;
+    dim3 grid((unsigned)blocks, (unsigned)batch);
     if (trans) {
-        if (unit) leaf_kernel<T, LEAF, NT, true, true><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info);
-        else leaf_kernel<T, LEAF, NT, true, false><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info);
+        if (unit) leaf_kernel<T, LEAF, NT, true, true><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info, bstride);
+        else leaf_kernel<T, LEAF, NT, true, false><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info, bstride);
     } else {
-        if (unit) leaf_kernel<T, LEAF, NT, false, true><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info);
-        else leaf_kernel<T, LEAF, NT, false, false><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info);
+        if (unit) leaf_kernel<T, LEAF, NT, false, true><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info, bstride);
+        else leaf_kernel<T, LEAF, NT, false, false><<<grid, NT, 0, c.stream>>>(a, lda, n, c.info, bstride);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_leaf_dispatch(const Ctx &c, bool trans, bool unit, int64_t n, T *a,
-                                 int64_t lda, int leaf) {
+                                 int64_t lda, int leaf, int64_t batch, int64_t bstride) {
     switch (leaf) {
-        case 16: return launch_leaf_t<T, 16>(c, trans, unit, n, a, lda);
-        case 32: return launch_leaf_t<T, 32>(c, trans, unit, n, a, lda);
-        case 64: return launch_leaf_t<T, 64>(c, trans, unit, n, a, lda);
+        case 16: return launch_leaf_t<T, 16>(c, trans, unit, n, a, lda, batch, bstride);
+        case 32: return launch_leaf_t<T, 32>(c, trans, unit, n, a, lda, batch, bstride);
+        case 64: return launch_leaf_t<T, 64>(c, trans, unit, n, a, lda, batch, bstride);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -130,14 +133,14 @@ cudaError_t launch_leaf_dispatch(const Ctx &c, bool trans, bool unit, int64_t n,
 }  // namespace
 
 cudaError_t launch_leaf(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
-                        int64_t lda, int leaf) {
+                        int64_t lda, int leaf, int64_t batch, int64_t bstride) {
     const int64_t nleaves = (n + leaf - 1) / leaf;
     const double nb = (double)leaf;
     TraceScope ts(c.stream, dt == TRI_F64 ? "leaf_f64" : "leaf_f32",
-                  (double)nleaves * nb * nb * nb / 3.0,
-                  2.0 * (double)n * nb / 2.0 * (dt == TRI_F64 ? 8.0 : 4.0));
-    if (dt == TRI_F64) return launch_leaf_dispatch<double>(c, trans, unit, n, (double *)a, lda, leaf);
-    return launch_leaf_dispatch<float>(c, trans, unit, n, (float *)a, lda, leaf);
+                  (double)batch * nleaves * nb * nb * nb / 3.0,
+                  (double)batch * 2.0 * (double)n * nb / 2.0 * (dt == TRI_F64 ? 8.0 : 4.0));
+    if (dt == TRI_F64) return launch_leaf_dispatch<double>(c, trans, unit, n, (double *)a, lda, leaf, batch, bstride);
+    return launch_leaf_dispatch<float>(c, trans, unit, n, (float *)a, lda, leaf, batch, bstride);
 }
 
 }  // namespace triinv

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
 // Rectangle rows x cols (column-major, lds) -> planes, with the triangle kind of the
 // operand applied (0 outside the stored triangle, 1 on an implicit unit diagonal).
 // Thread t owns rows 2*(t%32), 2*(t%32)+1 of a 64-row strip; blockIdx.y = 8-column group.
+template <bool TR>
 __global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict__ a, int64_t lds,
                                                          int64_t rows, int64_t cols, int kind,
                                                          __nv_bfloat16 *__restrict__ p0,
@@ -111,14 +112,16 @@ __global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict
     const int64_t i = (int64_t)blockIdx.x * 64 + 2 * lane;
     const int64_t j = (int64_t)blockIdx.y * 8 + w;
     if (i >= rows || j >= cols) return;
+    // element (r, j) of op(src): src itself, or its transpose (TR)
+    auto at = [&](int64_t r) -> float { return TR ? a[j + r * lds] : a[r + j * lds]; };
     auto fetch = [&](int64_t r) -> float {
         if (r >= rows) return 0.f;
         switch (kind) {
-            case 1: return j <= r ? a[r + j * lds] : 0.f;                        // lower
-            case 2: return j >= r ? a[r + j * lds] : 0.f;                        // upper
-            case 3: return j < r ? a[r + j * lds] : (j == r ? 1.f : 0.f);        // lower, unit
-            case 4: return j > r ? a[r + j * lds] : (j == r ? 1.f : 0.f);        // upper, unit
-            default: return a[r + j * lds];
+            case 1: return j <= r ? at(r) : 0.f;                        // lower
+            case 2: return j >= r ? at(r) : 0.f;                        // upper
+            case 3: return j < r ? at(r) : (j == r ? 1.f : 0.f);        // lower, unit
+            case 4: return j > r ? at(r) : (j == r ? 1.f : 0.f);        // upper, unit
+            default: return at(r);
         }
     };
     __nv_bfloat16 h0, m0, l0, h1, m1, l1;
@@ -143,11 +146,12 @@ __global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict
 
 cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t rows, int64_t cols,
                               int kind, __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
-                              int64_t ldp) {
+                              int64_t ldp, bool trans) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((cols + 7) / 8));
     TraceScope ts(c.stream, "split_rect", 0.0, (double)rows * cols * (4.0 + (p2 ? 6.0 : 4.0)));
-    split_rect_kernel<<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
+    if (trans) split_rect_kernel<true><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
+    else split_rect_kernel<false><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
     return cudaGetLastError();
 }
 

@@ -238,10 +238,12 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const int64_t gn = gn0 + j;
-            const bool keep = j < left && !(ep.cmask == 1 && gn > gm) && !(ep.cmask == 2 && gm > gn);
+            const bool low = ep.cmask == 1 || ep.cmask == 3, up = ep.cmask == 2 || ep.cmask == 4;
+            const bool keep = j < left && !(low && gn > gm) && !(up && gm > gn);
             if (keep) {
                 const float v = ep.alpha * __uint_as_float(r[j]);
-                ep.x[xo] = ep.beta == 0.f ? v : fmaf(ep.beta, ep.x[xo], v);
+                if (ep.cmask >= 3 && gm == gn) ep.x[xo] = 0.f;     // strict triangle: zero diagonal
+                else ep.x[xo] = ep.beta == 0.f ? v : fmaf(ep.beta, ep.x[xo], v);
             }
             xo += ep.ldx;
         }

@@ -36,7 +36,8 @@ struct Epi {
     int64_t ldo;
     int64_t mlim, nlim;            // output rows / columns that exist
     float alpha = 1.f, beta = 0.f; // MODE_GEN: x <- alpha * acc + beta * x
-    int cmask = 0;                 // MODE_GEN: 0 full, 1 lower, 2 upper part of x written
+    int cmask = 0;                 // MODE_GEN: part of x written: 0 full, 1 lower, 2 upper,
+                                   // 3 / 4 strict lower / upper with a zero diagonal
 };
 
 enum Mode {

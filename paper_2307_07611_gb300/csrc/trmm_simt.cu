@@ -43,14 +43,18 @@ __device__ __forceinline__ int micro_index(int t, int r) {
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool TRANS, bool UNIT, int MODE>
 __global__ void __launch_bounds__(Cfg<T, BM, BN, BK, TM, TN>::NT)
-trmm_level_kernel(T *__restrict__ a, int64_t lda, int64_t n, int64_t h, T *__restrict__ w) {
+trmm_level_kernel(T *__restrict__ a, int64_t lda, int64_t n, int64_t h, T *__restrict__ w,
+                  int64_t pairs, int64_t bstride) {
     using C = Cfg<T, BM, BN, BK, TM, TN>;
     constexpr int NT = C::NT;
     __shared__ __align__(16) T As[2][BK][BM + C::PAD];
     __shared__ __align__(16) T Bs[2][BK][BN + C::PAD];
 
     const int tid = threadIdx.x;
-    const int64_t q = blockIdx.z;
+    const int64_t bz = blockIdx.z / pairs;       // matrix of a strided batch
+    const int64_t q = blockIdx.z % pairs;
+    a += bz * bstride;
+    w += bz * pairs * h * h;
     const int64_t a0 = q * 2 * h;             // first row/col of the A block
     const int64_t c0 = a0 + h;                // first row/col of the C block
     const int64_t hc = min(h, n - c0);        // rows of C (ragged on the last pair)
@@ -178,33 +182,35 @@ trmm_level_kernel(T *__restrict__ a, int64_t lda, int64_t n, int64_t h, T *__res
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, int MODE>
 cudaError_t launch_cfg(const Ctx &c, bool trans, bool unit, int64_t n, T *a, int64_t lda,
-                       int64_t h, T *w) {
+                       int64_t h, T *w, int64_t batch, int64_t bstride) {
     using C = Cfg<T, BM, BN, BK, TM, TN>;
     const int64_t pairs = level_pairs(n, h);
-    if (pairs <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((h + BN - 1) / BN), (unsigned)((h + BM - 1) / BM), (unsigned)pairs);
+    if (pairs <= 0 || batch <= 0) return cudaSuccess;
+    if (pairs * batch > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((h + BN - 1) / BN), (unsigned)((h + BM - 1) / BM), (unsigned)(pairs * batch));
     if (trans) {
-        if (unit) trmm_level_kernel<T, BM, BN, BK, TM, TN, true, true, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w);
-        else trmm_level_kernel<T, BM, BN, BK, TM, TN, true, false, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w);
+        if (unit) trmm_level_kernel<T, BM, BN, BK, TM, TN, true, true, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w, pairs, bstride);
+        else trmm_level_kernel<T, BM, BN, BK, TM, TN, true, false, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w, pairs, bstride);
     } else {
-        if (unit) trmm_level_kernel<T, BM, BN, BK, TM, TN, false, true, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w);
-        else trmm_level_kernel<T, BM, BN, BK, TM, TN, false, false, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w);
+        if (unit) trmm_level_kernel<T, BM, BN, BK, TM, TN, false, true, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w, pairs, bstride);
+        else trmm_level_kernel<T, BM, BN, BK, TM, TN, false, false, MODE><<<grid, C::NT, 0, c.stream>>>(a, lda, n, h, w, pairs, bstride);
     }
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t launch_mode(const Ctx &c, bool trans, bool unit, int64_t n, T *a, int64_t lda,
-                        int64_t h, T *w) {
+                        int64_t h, T *w, int64_t batch, int64_t bstride) {
     if (sizeof(T) == 4 && h >= 128)
-        return launch_cfg<T, 128, 128, 8, 8, 8, MODE>(c, trans, unit, n, a, lda, h, w);
-    return launch_cfg<T, 64, 64, 16, 4, 4, MODE>(c, trans, unit, n, a, lda, h, w);
+        return launch_cfg<T, 128, 128, 8, 8, 8, MODE>(c, trans, unit, n, a, lda, h, w, batch, bstride);
+    return launch_cfg<T, 64, 64, 16, 4, 4, MODE>(c, trans, unit, n, a, lda, h, w, batch, bstride);
 }
 
 }  // namespace
 
 cudaError_t launch_trmm_level(const Ctx &c, tri_dtype dt, bool trans, bool unit, int mode,
-                              int64_t n, void *a, int64_t lda, int64_t h, void *w) {
+                              int64_t n, void *a, int64_t lda, int64_t h, void *w,
+                              int64_t batch, int64_t bstride) {
     const int64_t pairs = level_pairs(n, h);
     if (pairs <= 0) return cudaSuccess;
     // Algorithmic flops: mode 0 is hc x h times an h x h lower operand, 2*hc*sum(h-j);
@@ -222,13 +228,13 @@ cudaError_t launch_trmm_level(const Ctx &c, tri_dtype dt, bool trans, bool unit,
     }
     const char *name = dt == TRI_F64 ? (mode == 0 ? "trmm_f64_right" : "trmm_f64_left")
                                      : (mode == 0 ? "trmm_f32_right" : "trmm_f32_left");
-    TraceScope ts(c.stream, name, flops, bytes);
+    TraceScope ts(c.stream, name, flops * (double)batch, bytes * (double)batch);
     if (dt == TRI_F64) {
-        if (mode == 0) return launch_mode<double, 0>(c, trans, unit, n, (double *)a, lda, h, (double *)w);
-        return launch_mode<double, 1>(c, trans, unit, n, (double *)a, lda, h, (double *)w);
+        if (mode == 0) return launch_mode<double, 0>(c, trans, unit, n, (double *)a, lda, h, (double *)w, batch, bstride);
+        return launch_mode<double, 1>(c, trans, unit, n, (double *)a, lda, h, (double *)w, batch, bstride);
     }
-    if (mode == 0) return launch_mode<float, 0>(c, trans, unit, n, (float *)a, lda, h, (float *)w);
-    return launch_mode<float, 1>(c, trans, unit, n, (float *)a, lda, h, (float *)w);
+    if (mode == 0) return launch_mode<float, 0>(c, trans, unit, n, (float *)a, lda, h, (float *)w, batch, bstride);
+    return launch_mode<float, 1>(c, trans, unit, n, (float *)a, lda, h, (float *)w, batch, bstride);
 }
 
 }  // namespace triinv

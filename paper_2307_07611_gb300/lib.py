@@ -46,6 +46,15 @@ def _declare(lib):
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "gen_inv": ([i64, vp, i64, i32, vp], i32),
+        "tri_inv_strided_batched": ([i32, i32, i64, vp, i64, i64, i64, i32, vp], i32),
+        "tri_inv_strided_batched_workspace_size": ([i64, i64, i32], sz),
+        "tri_inv_strided_batched_ex": ([i32, i32, i64, vp, i64, i64, i64, i32, vp, sz, vp], i32),
+        "tri_inv_backward": ([i32, i32, i64, vp, i64, vp, i64, vp, i64, i32, vp], i32),
+        "tri_inv_backward_strided_batched": ([i32, i32, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64, i64,
+                                              i32, vp], i32),
+        "tri_inv_backward_workspace_size": ([i64, i64, i32], sz),
+        "tri_inv_backward_strided_batched_ex": ([i32, i32, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64,
+                                                 i64, i32, vp, sz, vp], i32),
         "tri_batched_plan_create": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32,
                                      ctypes.POINTER(vp)], i32),
         "tri_batched_exec": ([vp, vp], i32),
@@ -148,6 +157,39 @@ def tri_inv_batched(count, sizes, ptrs, uplo, diag, dtype, stream=0) -> int:
     return load().tri_inv_batched(count, sz, pt, uplo, diag, dtype, stream or None)
 
 
+def tri_inv_strided_batched(uplo, diag, n, ptr, ld, stride, batch, dtype, stream=0) -> int:
+    return load().tri_inv_strided_batched(uplo, diag, n, ptr, ld, stride, batch, dtype, stream or None)
+
+
+def tri_inv_strided_batched_workspace_size(n, batch, dtype) -> int:
+    return int(load().tri_inv_strided_batched_workspace_size(n, batch, dtype))
+
+
+def tri_inv_strided_batched_ex(uplo, diag, n, ptr, ld, stride, batch, dtype, workspace, ws_bytes, stream=0) -> int:
+    return load().tri_inv_strided_batched_ex(uplo, diag, n, ptr, ld, stride, batch, dtype, workspace or None,
+                                             ws_bytes, stream or None)
+
+
+def tri_inv_backward(uplo, diag, n, x, ldx, g, ldg, dt, lddt, dtype, stream=0) -> int:
+    return load().tri_inv_backward(uplo, diag, n, x, ldx, g, ldg, dt, lddt, dtype, stream or None)
+
+
+def tri_inv_backward_strided_batched(uplo, diag, n, x, ldx, sx, g, ldg, sg, dt, lddt, sd, batch, dtype,
+                                     stream=0) -> int:
+    return load().tri_inv_backward_strided_batched(uplo, diag, n, x, ldx, sx, g, ldg, sg, dt, lddt, sd, batch,
+                                                   dtype, stream or None)
+
+
+def tri_inv_backward_workspace_size(n, batch, dtype) -> int:
+    return int(load().tri_inv_backward_workspace_size(n, batch, dtype))
+
+
+def tri_inv_backward_strided_batched_ex(uplo, diag, n, x, ldx, sx, g, ldg, sg, dt, lddt, sd, batch, dtype,
+                                        workspace, ws_bytes, stream=0) -> int:
+    return load().tri_inv_backward_strided_batched_ex(uplo, diag, n, x, ldx, sx, g, ldg, sg, dt, lddt, sd, batch,
+                                                      dtype, workspace or None, ws_bytes, stream or None)
+
+
 TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -224,7 +266,17 @@ def _rowmajor_square(t):
 
 def inv_(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=None):
     """In place: the ``lower`` (or upper) triangle of the row-major CUDA tensor ``t``
-    becomes that of t^-1; the other triangle is not touched."""
+    (n x n, or a batch b x n x n with contiguous matrices) becomes that of t^-1; the other
+    triangle is not touched."""
+    if t.dim() == 3:
+        if not t.is_cuda or not t.is_contiguous() or t.shape[1] != t.shape[2]:
+            raise ValueError("expected a contiguous CUDA batch of square matrices")
+        b, n = t.shape[0], t.shape[1]
+        st = tri_inv_strided_batched(TRI_UPPER if lower else TRI_LOWER, TRI_UNIT if unit else TRI_NONUNIT, n,
+                                     t.data_ptr(), max(1, n), n * n, b, _dtype_code(t, mixed),
+                                     _stream_handle(stream))
+        check(st, "tri_inv_strided_batched")
+        return t
     _rowmajor_square(t)
     n = t.shape[0]
     # Row-major lower == column-major upper with lda = stride(0).
@@ -233,6 +285,58 @@ def inv_(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=
                  _dtype_code(t, mixed), _stream_handle(stream))
     check(st, "tri_inv")
     return t
+
+
+def inv_grad(x, g, lower: bool = True, unit: bool = False, mixed: bool = False, stream=None):
+    """dL/dT = -P(X^T G X^T) for X = T^-1 (row-major CUDA tensors, n x n or b x n x n).
+    The result has zeros outside T's free entries."""
+    import torch
+    x = x.contiguous()
+    g = g.contiguous()
+    out = torch.zeros_like(x)
+    n = x.shape[-1]
+    b = x.shape[0] if x.dim() == 3 else 1
+    # Row-major buffers are the column-major transposes: flip the triangle.
+    uplo = TRI_UPPER if lower else TRI_LOWER
+    st = tri_inv_backward_strided_batched(uplo, TRI_UNIT if unit else TRI_NONUNIT, n, x.data_ptr(), n, n * n,
+                                          g.data_ptr(), n, n * n, out.data_ptr(), n, n * n, b,
+                                          _dtype_code(x, mixed), _stream_handle(stream))
+    check(st, "tri_inv_backward")
+    return out
+
+
+def _tri_inv_function():
+    import torch
+
+    class TriInv(torch.autograd.Function):
+        """X = T^-1 for a triangular T (n x n or b x n x n CUDA tensor); the backward pass
+        is the library's adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, t, lower=True, unit=False, mixed=False):
+            x = inv(t, lower=lower, unit=unit, mixed=mixed)
+            ctx.save_for_backward(x)
+            ctx.flags = (lower, unit, mixed)
+            return x
+
+        @staticmethod
+        def backward(ctx, g):
+            (x,) = ctx.saved_tensors
+            lower, unit, mixed = ctx.flags
+            return inv_grad(x, g, lower=lower, unit=unit, mixed=mixed), None, None, None
+
+    return TriInv
+
+
+_TRI_INV_FN = None
+
+
+def tri_inv_autograd(t, lower: bool = True, unit: bool = False, mixed: bool = False):
+    """Differentiable triangular inverse (torch.autograd.Function over the C ABI)."""
+    global _TRI_INV_FN
+    if _TRI_INV_FN is None:
+        _TRI_INV_FN = _tri_inv_function()
+    return _TRI_INV_FN.apply(t, lower, unit, mixed)
 
 
 def general_inv(a, mixed: bool = False, stream=None):
@@ -255,5 +359,5 @@ def inv(t, lower: bool = True, unit: bool = False, mixed: bool = False, stream=N
     inv_(out, lower=lower, unit=unit, mixed=mixed, stream=stream)
     out = torch.tril(out) if lower else torch.triu(out)
     if unit:
-        out.diagonal().fill_(1)
+        out.diagonal(dim1=-2, dim2=-1).fill_(1)
     return out
