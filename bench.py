@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-quality", action="store_true",
                    help="skip the residual / oracle check (for profiler launch lists)")
     p.add_argument("--cpu-sample-stride", type=int, default=1)
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
     return p.parse_args()
 
 
@@ -165,6 +167,111 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ---- secondary workloads (the other rows of the hot path) ----------------------------------
+
+def event_time(torch, fn, reps, warmup=1, setup=None):
+    """Median CUDA-event time (ms) of fn() over `reps` runs after `warmup`; setup() runs
+    before each run, outside the timed interval."""
+    ms = []
+    stream = torch.cuda.current_stream()
+    for i in range(warmup + reps):
+        if setup:
+            setup()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def secondary(torch, lib, dev):
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    out = {}
+    sh = int(torch.cuda.current_stream().cuda_stream)
+
+    # single lower FP64 n = 512 (uniform law, seed 0), plain recursion, leaf 64
+    n = 512
+    t = inputs.tri_lower(n, seed=0, law="uniform")
+    pr = torch.from_numpy(np.ascontiguousarray(t.T)).to(dev)
+    wk = torch.empty_like(pr)
+    ms = event_time(torch, lambda: lib.check(lib.tri_inv(0, 0, n, wk.data_ptr(), n, lib.TRI_F64, sh)), 20, 3,
+                    setup=lambda: wk.copy_(pr))
+    xd = wk.T.tril()
+    td = pr.T.tril()
+    r = td @ xd
+    r.diagonal().sub_(1.0)
+    out["single_f64_n512"] = {"value": n ** 3 / 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (n^3/3)", "ms": ms,
+                              "residual": float(r.norm() / (td.norm() * xd.norm()))}
+
+    # general dense FP32 n = 16384: A = N(0,1)/sqrt(n) + 2I, block LU then U^-1 L^-1
+    n = 16384
+    a = inputs.general(n, seed=0, dtype=np.float32)
+    pr = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
+    wk = torch.empty_like(pr)
+    res = {}
+    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32)):
+        need = lib.gen_inv_workspace_size(n, code)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        ms = event_time(torch, lambda: lib.check(lib.gen_inv_ex(n, wk.data_ptr(), n, code, wp, need, sh)),
+                        2 if name == "mixed" else 1, 1, setup=lambda: wk.copy_(pr))
+        cols = [0, 8191, 16383]
+        x = wk[cols, :].double()                       # rows of the buffer = columns of X
+        ad = pr.T.double()
+        rr = ad @ x.T
+        for k, c in enumerate(cols):
+            rr[c, k] -= 1.0
+        cres = max(float(rr[:, k].norm() / (ad.norm() * x[k].norm())) for k in range(len(cols)))
+        res[name] = {"value": n ** 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (n^3)", "ms": ms,
+                     "sampled_column_residual_max": cres}
+        del ws
+    out["general_f32_n16384"] = res
+    del pr, wk
+
+    # batched: 4096 lower FP32 blocks, sizes U{16..256}, one persistent graph-captured launch
+    sizes, blocks = inputs.batched_blocks(4096, seed=0, dtype=np.float32)
+    host = np.concatenate([b.T.reshape(-1) for b in blocks]).astype(np.float32)
+    pr = torch.from_numpy(host).to(dev)
+    wk = torch.empty_like(pr)
+    offs = np.cumsum([0] + [int(k) * int(k) for k in sizes[:-1]])
+    ptrs = [wk.data_ptr() + 4 * int(o) for o in offs]
+    st, plan = lib.tri_batched_plan_create(len(sizes), sizes, ptrs, 0, 0, lib.TRI_F32)
+    lib.check(st, "tri_batched_plan_create")
+    ms = event_time(torch, lambda: lib.check(lib.tri_batched_exec(plan, sh)), 10, 3, setup=lambda: wk.copy_(pr))
+    fl = float(sum(float(k) ** 3 / 3 for k in sizes))
+    out["batched_4096"] = {"value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (sum n^3/3)", "ms": ms,
+                           "threads": lib.tri_batched_plan_threads(plan),
+                           "dense_bytes_GBps": 2 * host.nbytes / (ms * 1e-3) / 1e9}
+    lib.tri_batched_plan_destroy(plan)
+    del pr, wk
+
+    # differentiation: batch 256 of n = 1024 FP32 lower (uniform law), loss sum(W * T^-1)
+    b, n = 256, 1024
+    ts, ws_ = inputs.adjoint_batch(b, n, seed=0)
+    pr = torch.from_numpy(np.ascontiguousarray(np.transpose(ts, (0, 2, 1)))).to(dev)
+    g = torch.from_numpy(np.ascontiguousarray(np.transpose(ws_, (0, 2, 1)))).to(dev)
+    wk = torch.empty_like(pr)
+    dt = torch.zeros_like(pr)
+    adj = {}
+    for name, code in (("plain", lib.TRI_F32), ("mixed", lib.TRI_F32_MIXED)):
+        fms = event_time(torch, lambda: lib.check(lib.tri_inv_strided_batched(
+            0, 0, n, wk.data_ptr(), n, n * n, b, code, sh)), 3, 1, setup=lambda: wk.copy_(pr))
+        bms = event_time(torch, lambda: lib.check(lib.tri_inv_backward_strided_batched(
+            0, 0, n, wk.data_ptr(), n, n * n, g.data_ptr(), n, n * n, dt.data_ptr(), n, n * n, b, code, sh)), 3, 1)
+        adj[name] = {"forward_ms": fms, "forward_value": b * n ** 3 / 3 / (fms * 1e-3) / 1e12,
+                     "backward_ms": bms, "backward_value": b * 4 * n ** 3 / 3 / (bms * 1e-3) / 1e12,
+                     "unit": "TFLOP/s (n^3/3 forward, 4n^3/3 backward, per matrix)"}
+    out["adjoint_256x1024"] = adj
+    del pr, g, wk, dt
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---- our arm ----------------------------------------------------------------------------
@@ -350,6 +457,10 @@ def main():
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": ms / k}
 
+    configs = None
+    if not args.no_configs:
+        configs = secondary(torch, lib, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, threads, sample = oracle_sample(n, args.cpu_sample_stride)
@@ -374,6 +485,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "per_step_ms_min": min(per_ms), "per_step_ms_median": statistics.median(per_ms),
             "trace": trace,
+            "configs": configs,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -10,11 +10,12 @@
 //        W   = B X_A       3 terms  hi*hi + hi*mid + mid*hi   -> W_hi, W_mid
 //        X21 = -X_C W      3 terms                              -> X (FP32) and its planes
 // 5. Newton-Schulz step X <- X (2I - T X) = X + X R:
-//        R = I - T X       6 terms (hh, hm, mh, hl, mm, lh): ~2^-24 relative accuracy;
-//                          R is a difference of nearly equal terms, of the order of the
-//                          3-term error (~1e-5), and is stored as hi/mid planes
-//        X += X R          3 terms: a 1-term BF16 product would leave an error of
-//                          2^-8 |X R| ~ 4e-8 normwise, above plain FP32's residual
+//        R = I - T X       6 terms (hh, hm, mh, hl, mm, lh) with FP32 promotion of the
+//                          tensor-core partial sums every 256 k: R is a difference of
+//                          nearly equal terms and needs ~2^-24 relative accuracy
+//        X += X R          1 term: R is as small as the forward residual (~3e-8
+//                          normwise at n = 8192), so the BF16 error 2^-8 |X R| of the
+//                          update adds ~1e-10, far below FP32 rounding
 // The tile lists of every product depend on n only and are built once per (device, n)
 // and kept in device memory.
 #include <algorithm>
@@ -57,7 +58,7 @@ Layout layout(int64_t n) {
     L.off_t = 0;
     L.off_x = L.off_t + 3 * al(plane);
     L.off_r = L.off_x + 3 * al(plane);
-    L.off_w = L.off_r + 2 * al(plane);
+    L.off_w = L.off_r + al(plane);
     L.off_s = L.off_w + 2 * al((size_t)L.wmax * 2);
     L.total = L.off_s + al(sbytes);
     return L;
@@ -140,8 +141,8 @@ tri_status build_plan(int dev, int sm_count, int64_t n, Plan **out) {
                 v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
                                      (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
         }
-        add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 3.0) * lower_prod,
-            pass == 0 ? 6 : 3);
+        add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 1.0) * lower_prod,
+            pass == 0 ? 6 : 1);
     }
     if (!v.empty()) {
         const size_t tb = v.size() * sizeof(tc::Tile), ob = offs.size() * sizeof(int);
@@ -180,13 +181,12 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     const Layout L = layout(n);
     uint8_t *base = (uint8_t *)ws;
     const size_t plane = ((size_t)L.ldp * (size_t)n * 2 + 255) / 256 * 256;
-    __nv_bfloat16 *T[3], *X[3], *R[2], *W[2];
+    __nv_bfloat16 *T[3], *X[3], *R[1], *W[2];
     for (int i = 0; i < 3; ++i) {
         T[i] = (__nv_bfloat16 *)(base + L.off_t + i * plane);
         X[i] = (__nv_bfloat16 *)(base + L.off_x + i * plane);
     }
     R[0] = (__nv_bfloat16 *)(base + L.off_r);
-    R[1] = (__nv_bfloat16 *)(base + L.off_r + plane);
     const size_t wplane = ((size_t)L.wmax * 2 + 255) / 256 * 256;
     W[0] = (__nv_bfloat16 *)(base + L.off_w);
     W[1] = (__nv_bfloat16 *)(base + L.off_w + wplane);
@@ -230,13 +230,14 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     }
     // 5. Newton-Schulz: R = I - T X, then X += X R
     const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
-    tc::Epi er{nullptr, 0, R[0], R[1], nullptr, L.ldp, n, n};
+    tc::Epi er{nullptr, 0, R[0], nullptr, nullptr, L.ldp, n, n};
     if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
                       plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
         return TRI_ERR_CUDA;
-    const tc::Plane rp[2] = {pl(R[0], n, n, L.ldp), pl(R[1], n, n, L.ldp)};
+    const tc::Plane rp[1] = {pl(R[0], n, n, L.ldp)};
+    const tc::Terms one{1, {0}, {0}};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
-    if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 2, rp, 2, three, plan->d_tiles + plan->upd.first,
+    if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + plan->upd.first,
                       plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
         return TRI_ERR_CUDA;
     return TRI_OK;

@@ -6,7 +6,7 @@
 // mixed-precision path:
 //   level products of the split (block inverse, proof of the main Theorem, Section 3):
 //       W = B X_A (3 terms)  and  X21 = -X_C W (3 terms);
-//   the Newton-Schulz step X <- X + X (I - T X): R = I - T X (6 terms), X += X R (3 terms).
+//   the Newton-Schulz step X <- X + X (I - T X): R = I - T X (6 terms), X += X R (1 term).
 //
 // Structure (one CTA per SM, persistent over a host-built tile list, longest first):
 //   warp 0      TMA producer: per (k-block, term) one pipeline slot = A tile 128x64
@@ -218,7 +218,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
                 const float r1 = v - __bfloat162float(h);
                 const __nv_bfloat16 m = __float2bfloat16_rn(r1);
                 ep.o0[off] = h;
-                ep.o1[off] = m;
+                if (MODE != MODE_RES || ep.o1) ep.o1[off] = m;
                 if (MODE == MODE_X21) ep.o2[off] = __float2bfloat16_rn(r1 - __bfloat162float(m));
             }
             off += ep.ldo;

@@ -43,7 +43,7 @@ struct Epi {
 enum Mode {
     MODE_W = 0,      // o0/o1 <- hi/lo BF16 split of acc                    (W = B X_A)
     MODE_X21 = 1,    // x <- -acc; o0/o1/o2 <- hi/mid/lo split of -acc      (X21 = -X_C W)
-    MODE_RES = 2,    // o0/o1 <- hi/lo split of I - acc (lower), 0 above    (R = I - T X)
+    MODE_RES = 2,    // o0 (o1) <- hi (lo) split of I - acc (lower), 0 above (R = I - T X)
     MODE_UPD = 3,    // x += acc on the lower triangle                       (X += X R)
     MODE_F32 = 4,    // x <- acc (plain column-major store, no view)        (verification)
     MODE_GEN = 5,    // x <- alpha acc + beta x, column-major, masked        (general products)
