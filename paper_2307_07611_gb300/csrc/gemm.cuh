@@ -31,6 +31,8 @@ struct GemmArgs {
     bool ta = false, tb = false;              // use A^T / B^T (stored column-major)
     int64_t batch = 1;                        // independent products, pointers advanced by
     int64_t sa = 0, sb = 0, sc = 0;           // these strides (elements)
+    int64_t batch2 = 1;                       // an outer batch level (product index =
+    int64_t sa2 = 0, sb2 = 0, sc2 = 0;        // inner + batch * outer)
 };
 
 double gemm_flops(const GemmArgs &g);

@@ -44,73 +44,97 @@ template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
 __global__ void __launch_bounds__(GCfg<T, BM, BN, BK, TM, TN>::NT)
 gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__ A, int64_t lda,
                  int akind, const T *__restrict__ B, int64_t ldb, int bkind, T beta, T *C,
-                 int64_t ldc, int cmask, int64_t sa, int64_t sb, int64_t sc) {
+                 int64_t ldc, int cmask, int64_t sa, int64_t sb, int64_t sc, int64_t nb1,
+                 int64_t sa2, int64_t sb2, int64_t sc2) {
     using Cf = GCfg<T, BM, BN, BK, TM, TN>;
     constexpr int NT = Cf::NT;
     __shared__ __align__(16) T As[2][BK][BM + Cf::PAD];
     __shared__ __align__(16) T Bs[2][BK][BN + Cf::PAD];
     const int tid = threadIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.y * BM;
-    const int64_t n0 = (int64_t)blockIdx.x * BN;
+    const int m0 = blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
     if (m0 >= M || n0 >= N) return;
-    A += (int64_t)blockIdx.z * sa;
-    B += (int64_t)blockIdx.z * sb;
-    C += (int64_t)blockIdx.z * sc;
+    {
+        const int64_t inner = blockIdx.z % nb1, outer = blockIdx.z / nb1;
+        A += inner * sa + outer * sa2;
+        B += inner * sb + outer * sb2;
+        C += inner * sc + outer * sc2;
+    }
     // Output mask: skip tiles entirely outside the stored triangle.
     const bool c_low = cmask == OP_LOWER || cmask == OP_LOWER_UNIT;
     const bool c_up = cmask == OP_UPPER || cmask == OP_UPPER_UNIT;
     if (c_low && n0 > m0 + BM - 1) return;
     if (c_up && m0 > n0 + BN - 1) return;
 
-    int64_t kbeg = 0, kend = K;
+    int kbeg = 0, kend = (int)K;
     const bool a_low = (akind == OP_LOWER || akind == OP_LOWER_UNIT);
     const bool a_up = (akind == OP_UPPER || akind == OP_UPPER_UNIT);
     const bool b_low = (bkind == OP_LOWER || bkind == OP_LOWER_UNIT);
     const bool b_up = (bkind == OP_UPPER || bkind == OP_UPPER_UNIT);
-    if (a_low) kend = min(kend, m0 + BM);          // A(m,k) = 0 for k > m
-    if (a_up) kbeg = max(kbeg, (m0 / BK) * BK);    // A(m,k) = 0 for k < m
-    if (b_low) kbeg = max(kbeg, (n0 / BK) * BK);   // B(k,n) = 0 for k < n
-    if (b_up) kend = min(kend, n0 + BN);           // B(k,n) = 0 for k > n
+    const bool a_unit = akind == OP_LOWER_UNIT || akind == OP_UPPER_UNIT;
+    const bool b_unit = bkind == OP_LOWER_UNIT || bkind == OP_UPPER_UNIT;
+    if (a_low) kend = min(kend, m0 + BM);          // op(A)(m,k) = 0 for k > m
+    if (a_up) kbeg = max(kbeg, (m0 / BK) * BK);    // op(A)(m,k) = 0 for k < m
+    if (b_low) kbeg = max(kbeg, (n0 / BK) * BK);   // op(B)(k,n) = 0 for k < n
+    if (b_up) kend = min(kend, n0 + BN);           // op(B)(k,n) = 0 for k > n
+
+    // Thread -> element maps follow the contiguous index of each operand in memory.
+    // Each thread keeps a pointer per loaded element and advances it by one k-slice per
+    // step; the masks are 32-bit compares.
+    int am[Cf::A_PER], ak[Cf::A_PER], bk[Cf::B_PER], bn[Cf::B_PER];
+    const T *pa[Cf::A_PER];
+    const T *pb[Cf::B_PER];
+    const int64_t a_kstep = TA ? 1 : lda, b_kstep = TB ? ldb : 1;
+#pragma unroll
+    for (int r = 0; r < Cf::A_PER; ++r) {
+        const int idx = tid + r * NT;
+        if (TA) { ak[r] = idx % BK; am[r] = idx / BK; }
+        else { am[r] = idx % BM; ak[r] = idx / BM; }
+        const int64_t gm = m0 + am[r], gk = kbeg + ak[r];
+        pa[r] = A + (TA ? (gk + gm * lda) : (gm + gk * lda));
+        am[r] += m0;
+    }
+#pragma unroll
+    for (int r = 0; r < Cf::B_PER; ++r) {
+        const int idx = tid + r * NT;
+        if (TB) { bn[r] = idx % BN; bk[r] = idx / BN; }
+        else { bk[r] = idx % BK; bn[r] = idx / BK; }
+        const int64_t gk = kbeg + bk[r], gn = n0 + bn[r];
+        pb[r] = B + (TB ? (gn + gk * ldb) : (gk + gn * ldb));
+        bn[r] += n0;
+    }
+    const int Mi = (int)M, Ni = (int)N;
 
     T ra[Cf::A_PER], rb[Cf::B_PER];
-    // Thread -> element maps follow the contiguous index of each operand in memory.
-    auto amap = [&](int idx, int &m, int &k) {
-        if (TA) { k = idx % BK; m = idx / BK; }
-        else { m = idx % BM; k = idx / BM; }
-    };
-    auto bmap = [&](int idx, int &k, int &nn) {
-        if (TB) { nn = idx % BN; k = idx / BN; }
-        else { k = idx % BK; nn = idx / BK; }
-    };
-    auto gload = [&](int64_t kt) {
+    auto gload = [&](int kt) {
 #pragma unroll
         for (int r = 0; r < Cf::A_PER; ++r) {
-            int m, k;
-            amap(tid + r * NT, m, k);
-            const int64_t gm = m0 + m, gk = kt + k;
-            ra[r] = (gm < M && gk < kend) ? tri_fetch(A, lda, TA, akind, gm, gk) : T(0);
+            const int m = am[r], k = kt + ak[r];
+            bool ok = m < Mi && k < kend;
+            if (a_low) ok = ok && k <= m;
+            if (a_up) ok = ok && k >= m;
+            T v = ok ? *pa[r] : T(0);
+            if (a_unit && k == m) v = T(1);
+            ra[r] = v;
+            pa[r] += BK * a_kstep;
         }
 #pragma unroll
         for (int r = 0; r < Cf::B_PER; ++r) {
-            int k, nn;
-            bmap(tid + r * NT, k, nn);
-            const int64_t gk = kt + k, gn = n0 + nn;
-            rb[r] = (gn < N && gk < kend) ? tri_fetch(B, ldb, TB, bkind, gk, gn) : T(0);
+            const int k = kt + bk[r], nn = bn[r];
+            bool ok = nn < Ni && k < kend;
+            if (b_low) ok = ok && k >= nn;
+            if (b_up) ok = ok && k <= nn;
+            T v = ok ? *pb[r] : T(0);
+            if (b_unit && k == nn) v = T(1);
+            rb[r] = v;
+            pb[r] += BK * b_kstep;
         }
     };
     auto sstore = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < Cf::A_PER; ++r) {
-            int m, k;
-            amap(tid + r * NT, m, k);
-            As[buf][k][m] = ra[r];
-        }
+        for (int r = 0; r < Cf::A_PER; ++r) As[buf][ak[r]][am[r] - m0] = ra[r];
 #pragma unroll
-        for (int r = 0; r < Cf::B_PER; ++r) {
-            int k, nn;
-            bmap(tid + r * NT, k, nn);
-            Bs[buf][k][nn] = rb[r];
-        }
+        for (int r = 0; r < Cf::B_PER; ++r) Bs[buf][bk[r]][bn[r] - n0] = rb[r];
     };
     const int tx = tid % (BN / TN), ty = tid / (BN / TN);
     T acc[TM][TN];
@@ -124,7 +148,7 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
         sstore(0);
         __syncthreads();
     }
-    for (int64_t kt = kbeg; kt < kend; kt += BK) {
+    for (int kt = kbeg; kt < kend; kt += BK) {
         const bool more = kt + BK < kend;
         if (more) gload(kt + BK);
 #pragma unroll
@@ -147,15 +171,15 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-        const int64_t gm = m0 + gmicro<BM, TM>(ty, i);
-        if (gm >= M) continue;
+        const int gm = m0 + gmicro<BM, TM>(ty, i);
+        if (gm >= Mi) continue;
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-            const int64_t gn = n0 + gmicro<BN, TN>(tx, j);
-            if (gn >= N) continue;
+            const int gn = n0 + gmicro<BN, TN>(tx, j);
+            if (gn >= Ni) continue;
             if (c_low && gn > gm) continue;
             if (c_up && gm > gn) continue;
-            T *c = C + gm + gn * ldc;
+            T *c = C + gm + (int64_t)gn * ldc;
             if ((cmask == OP_LOWER_UNIT || cmask == OP_UPPER_UNIT) && gm == gn) {
                 *c = T(0);
                 continue;
@@ -168,10 +192,10 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
 cudaError_t launch_g2(const Ctx &c, const GemmArgs &g) {
     using Cf = GCfg<T, BM, BN, BK, TM, TN>;
-    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM), (unsigned)g.batch);
+    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM), (unsigned)(g.batch * g.batch2));
     gemm_simt_kernel<T, BM, BN, BK, TM, TN, TA, TB><<<grid, Cf::NT, 0, c.stream>>>(
         g.m, g.n, g.k, (T)g.alpha, (const T *)g.a, g.lda, g.akind, (const T *)g.b, g.ldb, g.bkind,
-        (T)g.beta, (T *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc);
+        (T)g.beta, (T *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc, g.batch, g.sa2, g.sb2, g.sc2);
     return cudaGetLastError();
 }
 
@@ -199,9 +223,10 @@ double gemm_flops(const GemmArgs &g) {
 }
 
 cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name) {
-    if (g.m <= 0 || g.n <= 0 || g.batch <= 0) return cudaSuccess;
-    if (g.batch > 65535) return cudaErrorInvalidValue;
-    TraceScope ts(c.stream, trace_name, gemm_flops(g) * (double)g.batch, 0.0);
+    if (g.m <= 0 || g.n <= 0 || g.batch <= 0 || g.batch2 <= 0) return cudaSuccess;
+    if (g.batch * g.batch2 > 65535 || g.m >= (1ll << 31) || g.n >= (1ll << 31) || g.k >= (1ll << 31))
+        return cudaErrorInvalidValue;
+    TraceScope ts(c.stream, trace_name, gemm_flops(g) * (double)(g.batch * g.batch2), 0.0);
     if (dt == TRI_F64) return launch_g<double, 64, 64, 16, 4, 4>(c, g);
     if (g.m >= 128 && g.n >= 128) return launch_g<float, 128, 128, 8, 8, 8>(c, g);
     return launch_g<float, 64, 64, 16, 4, 4>(c, g);
