@@ -24,6 +24,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 struct tri_batched_plan;   // opaque to callers (include/triinv.h)
@@ -80,17 +82,17 @@ __device__ __forceinline__ void warp_store32(T *C, const T (&acc)[4][8], int lan
 }
 
 // In-place inverse of a lower 32 x 32 tile by one warp (column recurrence; lane j owns
-// column j).  Returns true if a pivot among the first `valid` rows is zero or non-finite.
+// column j).  Returns the first row (< valid) whose pivot is zero or non-finite, or 32.
 template <typename T>
-__device__ __forceinline__ bool warp_tile_inverse(T *t, int lane, int valid) {
+__device__ __forceinline__ int warp_tile_inverse(T *t, int lane, int valid) {
     T x[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) x[i] = T(0);
-    bool bad = false;
+    int bad = 32;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         const T tkk = t[k * TP + k];
-        if (k < valid && (tkk == T(0) || !isfinite(tkk))) bad = true;
+        if (k < valid && bad == 32 && (tkk == T(0) || !isfinite(tkk))) bad = k;
         const T dk = T(1) / tkk;
         // row k of the inverse becomes final
         if (lane == k) x[k] = dk;
@@ -106,129 +108,176 @@ __device__ __forceinline__ bool warp_tile_inverse(T *t, int lane, int valid) {
     return bad;
 }
 
+// Inverts one block held in global memory (column-major view, order d.n <= 32 * MAXT) in
+// shared memory and writes the lower triangle back.  row0 >= 0: the block is the
+// diagonal block starting at row row0 of a larger matrix (pivot errors report the row,
+// and the BF16 hi/mid/lo planes of the whole block are written when p0 != nullptr);
+// row0 < 0: a block of a batch (pivot errors report d.index).
+template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
+__device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
+                                             __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
+                                             long long ldp, long long ntot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+    const int n = d.n, nt = (n + 31) / 32;
+    const T *g = reinterpret_cast<const T *>(d.ptr);
+    const long long ld = d.ld;
+
+    // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
+    // One warp per tile, 32 independent loads in flight per lane.
+    const int ntl = nt * (nt + 1) / 2;
+    for (int tl = warp; tl < ntl; tl += nwarps) {
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+        const int J = tl - I * (I + 1) / 2;
+        T v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            // lane = row (column-major source) or column (transposed source)
+            const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+            const int gi = I * 32 + r, gj = J * 32 + c;
+            if (gi < n && gj < n) {
+                if (gj < gi) v[q] = g[vidx<TRANS>(gi, gj, ld)];
+                else if (gj == gi) v[q] = UNIT ? T(1) : g[vidx<TRANS>(gi, gi, ld)];
+                else v[q] = T(0);
+            } else {
+                v[q] = (gi == gj) ? T(1) : T(0);
+            }
+        }
+        T *tp = tile_ptr(tiles, I, J);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+            tp[r * TP + c] = v[q];
+        }
+    }
+    __syncthreads();
+
+    // Diagonal tiles.
+    for (int I = warp; I < nt; I += nwarps) {
+        const int bad = warp_tile_inverse(tile_ptr(tiles, I, I), lane, min(32, n - I * 32));
+        if (bad < 32 && lane == 0 && !UNIT)
+            atomicMin(info, row0 >= 0 ? (long long)(row0 + I * 32 + bad) : (long long)d.index);
+    }
+    __syncthreads();
+
+    // Split levels (in tiles): ht = 1, 2, 4.
+    for (int ht = 1; ht < nt; ht *= 2) {
+        const int pairs = (nt - ht + 2 * ht - 1) / (2 * ht);
+        // W_q(Iw, Jw) = sum_{K >= Jw} B(c0 + Iw, a0 + K) X(a0 + K, a0 + Jw)
+        int jobs = 0;
+        for (int q = 0; q < pairs; ++q) jobs += min(ht, nt - (2 * q * ht + ht)) * ht;
+        for (int jb = warp; jb < jobs; jb += nwarps) {
+            int q = 0, rest = jb;
+            for (;;) {
+                const int hc = min(ht, nt - (2 * q * ht + ht));
+                if (rest < hc * ht) break;
+                rest -= hc * ht;
+                ++q;
+            }
+            const int a0 = 2 * q * ht, c0 = a0 + ht;
+            const int Iw = rest / ht, Jw = rest % ht;
+            T acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+            for (int K = Jw; K < ht; ++K)
+                warp_mma32(tile_ptr(tiles, c0 + Iw, a0 + K), tile_ptr(tiles, a0 + K, a0 + Jw), acc, lane);
+            warp_store32(wt + (size_t)jb * TE, acc, lane, T(1));
+        }
+        __syncthreads();
+        // B(c0 + Iw, a0 + Jw) <- -sum_{K <= Iw} X_C(c0 + Iw, c0 + K) W_q(K, Jw)
+        for (int jb = warp; jb < jobs; jb += nwarps) {
+            int q = 0, rest = jb, base = 0;
+            for (;;) {
+                const int hc = min(ht, nt - (2 * q * ht + ht));
+                if (rest < hc * ht) break;
+                rest -= hc * ht;
+                base += hc * ht;
+                ++q;
+            }
+            const int a0 = 2 * q * ht, c0 = a0 + ht;
+            const int Iw = rest / ht, Jw = rest % ht;
+            T acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+            for (int K = 0; K <= Iw; ++K)
+                warp_mma32(tile_ptr(tiles, c0 + Iw, c0 + K), wt + (size_t)(base + K * ht + Jw) * TE, acc, lane);
+            warp_store32(tile_ptr(tiles, c0 + Iw, a0 + Jw), acc, lane, T(-1));
+        }
+        __syncthreads();
+    }
+
+    // Store the lower triangle back (unit diagonal not written), one warp per tile.
+    T *go = reinterpret_cast<T *>(d.ptr);
+    for (int tl = warp; tl < ntl; tl += nwarps) {
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+        const int J = tl - I * (I + 1) / 2;
+        const T *tp = tile_ptr(tiles, I, J);
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const int r = TRANS ? q : lane, c = TRANS ? lane : q;
+            const int gi = I * 32 + r, gj = J * 32 + c;
+            if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = tp[r * TP + c];
+        }
+    }
+    if (p0 != nullptr) {
+        // BF16 planes of the whole diagonal block (the strict upper part as zeros).
+        for (int e = warp; e < nt * nt; e += nwarps) {
+            const int I = e / nt, J = e % nt;
+            const T *tp = I >= J ? tile_ptr(tiles, I, J) : nullptr;
+#pragma unroll 4
+            for (int c = 0; c < 32; ++c) {
+                const long long gi = row0 + I * 32 + lane, gj = row0 + J * 32 + c;
+                if (gi >= ntot || gj >= ntot || I * 32 + lane >= n || J * 32 + c >= n) continue;
+                const float v = tp ? (float)tp[lane * TP + c] : 0.f;
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                const float r1 = v - __bfloat162float(h);
+                const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                const long long o = gi + gj * ldp;
+                p0[o] = h;
+                p1[o] = m;
+                p2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            }
+        }
+    }
+}
+
 template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
 __global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict__ descs, int count, int *counter, long long *info) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T *tiles = reinterpret_cast<T *>(smem_raw);
     T *wt = tiles + (size_t)BLimits<MAXT>::kTiles * TE;
     __shared__ int s_job;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = NT / 32;
-
+    const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s_job = atomicAdd(counter, 1);
         __syncthreads();
         const int job = s_job;
         __syncthreads();
         if (job >= count) break;
-        const BDesc d = descs[job];
-        const int n = d.n, nt = (n + 31) / 32;
-        const T *g = reinterpret_cast<const T *>(d.ptr);
-        const long long ld = d.ld;
-
-        // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
-        // One warp per tile, 32 independent loads in flight per lane.
-        const int ntl = nt * (nt + 1) / 2;
-        for (int tl = warp; tl < ntl; tl += nwarps) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-            const int J = tl - I * (I + 1) / 2;
-            T v[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                // lane = row (column-major source) or column (transposed source)
-                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
-                const int gi = I * 32 + r, gj = J * 32 + c;
-                if (gi < n && gj < n) {
-                    if (gj < gi) v[q] = g[vidx<TRANS>(gi, gj, ld)];
-                    else if (gj == gi) v[q] = UNIT ? T(1) : g[vidx<TRANS>(gi, gi, ld)];
-                    else v[q] = T(0);
-                } else {
-                    v[q] = (gi == gj) ? T(1) : T(0);
-                }
-            }
-            T *tp = tile_ptr(tiles, I, J);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
-                tp[r * TP + c] = v[q];
-            }
-        }
-        __syncthreads();
-
-        // Diagonal tiles.
-        for (int I = warp; I < nt; I += nwarps) {
-            const bool bad = warp_tile_inverse(tile_ptr(tiles, I, I), lane, min(32, n - I * 32));
-            if (bad && lane == 0 && !UNIT) atomicMin(info, (long long)d.index);
-        }
-        __syncthreads();
-
-        // Split levels (in tiles): ht = 1, 2, 4.
-        for (int ht = 1; ht < nt; ht *= 2) {
-            const int pairs = (nt - ht + 2 * ht - 1) / (2 * ht);
-            // W_q(Iw, Jw) = sum_{K >= Jw} B(c0 + Iw, a0 + K) X(a0 + K, a0 + Jw)
-            int jobs = 0;
-            for (int q = 0; q < pairs; ++q) jobs += min(ht, nt - (2 * q * ht + ht)) * ht;
-            for (int jb = warp; jb < jobs; jb += nwarps) {
-                int q = 0, rest = jb;
-                for (;;) {
-                    const int hc = min(ht, nt - (2 * q * ht + ht));
-                    if (rest < hc * ht) break;
-                    rest -= hc * ht;
-                    ++q;
-                }
-                const int a0 = 2 * q * ht, c0 = a0 + ht;
-                const int Iw = rest / ht, Jw = rest % ht;
-                T acc[4][8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
-                for (int K = Jw; K < ht; ++K)
-                    warp_mma32(tile_ptr(tiles, c0 + Iw, a0 + K), tile_ptr(tiles, a0 + K, a0 + Jw), acc, lane);
-                warp_store32(wt + (size_t)jb * TE, acc, lane, T(1));
-            }
-            __syncthreads();
-            // B(c0 + Iw, a0 + Jw) <- -sum_{K <= Iw} X_C(c0 + Iw, c0 + K) W_q(K, Jw)
-            for (int jb = warp; jb < jobs; jb += nwarps) {
-                int q = 0, rest = jb, base = 0;
-                for (;;) {
-                    const int hc = min(ht, nt - (2 * q * ht + ht));
-                    if (rest < hc * ht) break;
-                    rest -= hc * ht;
-                    base += hc * ht;
-                    ++q;
-                }
-                const int a0 = 2 * q * ht, c0 = a0 + ht;
-                const int Iw = rest / ht, Jw = rest % ht;
-                T acc[4][8];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
-                for (int K = 0; K <= Iw; ++K)
-                    warp_mma32(tile_ptr(tiles, c0 + Iw, c0 + K), wt + (size_t)(base + K * ht + Jw) * TE, acc, lane);
-                warp_store32(tile_ptr(tiles, c0 + Iw, a0 + Jw), acc, lane, T(-1));
-            }
-            __syncthreads();
-        }
-
-        // Store the lower triangle back (unit diagonal not written), one warp per tile.
-        T *go = reinterpret_cast<T *>(d.ptr);
-        for (int tl = warp; tl < ntl; tl += nwarps) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-            const int J = tl - I * (I + 1) / 2;
-            const T *tp = tile_ptr(tiles, I, J);
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) {
-                const int r = TRANS ? q : lane, c = TRANS ? lane : q;
-                const int gi = I * 32 + r, gj = J * 32 + c;
-                if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = tp[r * TP + c];
-            }
-        }
+        invert_block<T, TRANS, UNIT, MAXT, NT>(descs[job], tiles, wt, info, -1, nullptr, nullptr, nullptr, 0, 0);
         __syncthreads();
     }
+}
+
+// The diagonal blocks of one n x n matrix (lower view through TRANS): CTA b inverts rows
+// and columns [256 b, 256 b + 256) in shared memory and, when p0 != nullptr, writes the
+// BF16 planes of that diagonal block.
+template <bool TRANS, bool UNIT>
+__global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long lda, long long n, long long *info,
+                                                             __nv_bfloat16 *p0, __nv_bfloat16 *p1,
+                                                             __nv_bfloat16 *p2, long long ldp) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    float *tiles = reinterpret_cast<float *>(smem_raw);
+    float *wt = tiles + (size_t)BLimits<8>::kTiles * TE;
+    const long long r0 = (long long)blockIdx.x * 256;
+    BDesc d{a + vidx<TRANS>(r0, r0, lda), lda, (int)min(256ll, n - r0), (int)blockIdx.x};
+    invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n);
 }
 
 template <typename T, int MAXT>
@@ -255,6 +304,28 @@ KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *sme
 }
 
 }  // namespace
+
+// Inverts the 256 x 256 diagonal blocks of an n x n FP32 matrix in place (one CTA each)
+// and writes their BF16 planes (used by the mixed path).
+cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
+                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp) {
+    const int64_t blocks = (n + 255) / 256;
+    if (blocks <= 0) return cudaSuccess;
+    const size_t smem = smem_bytes<float, 8>();
+    auto k = trans ? (unit ? diag_blocks_kernel<true, true> : diag_blocks_kernel<true, false>)
+                   : (unit ? diag_blocks_kernel<false, true> : diag_blocks_kernel<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    double fl = 0.0;
+    for (int64_t b = 0; b < blocks; ++b) {
+        const double nb = (double)std::min<int64_t>(256, n - 256 * b);
+        fl += nb * nb * nb / 3.0;
+    }
+    TraceScope ts(c.stream, "diag_blocks", fl, (double)n * 256.0 * (4.0 + 4.0 + 6.0));
+    k<<<(unsigned)blocks, 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp);
+    return cudaGetLastError();
+}
+
 }  // namespace triinv
 
 struct tri_batched_plan {

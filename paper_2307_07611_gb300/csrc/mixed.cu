@@ -2,9 +2,9 @@
 // products, followed by one Newton-Schulz step.
 //
 // 1. T (FP32) -> BF16 planes T_hi, T_mid, T_lo                       (split.cu)
-// 2. every 256 x 256 diagonal block is inverted in FP32: CRIT leaves of 64 and the two
-//    lowest split levels on CUDA cores                                (leaf.cu, trmm_simt.cu)
-// 3. those diagonal blocks of X -> BF16 planes X_hi, X_mid, X_lo     (split.cu)
+// 2. every 256 x 256 diagonal block is inverted in FP32 by one CTA in shared memory
+//    (CRIT leaves of 32, split levels 32..128) and written with its BF16 planes
+//    X_hi, X_mid, X_lo                                                 (batched.cu)
 // 4. split levels h = 256, 512, ...: for every pair (block inverse of the proof of the
 //    main Theorem, Section 3; Algorithm COMBRIT with two blocks, Section 4.1)
 //        W   = B X_A       3 terms  hi*hi + hi*mid + mid*hi   -> W_hi, W_mid
@@ -30,6 +30,8 @@ namespace triinv {
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
                                 __nv_bfloat16 *p2, int64_t ldp);
+cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
+                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp);
 
 namespace {
 
@@ -199,11 +201,10 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     // 1. T planes
     if (launch_split_planes(c, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp) != cudaSuccess)
         return TRI_ERR_CUDA;
-    // 2. FP32 diagonal blocks of 256
-    st = run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, scratch, kDiag);
-    if (st != TRI_OK) return st;
-    // 3. their planes
-    if (launch_split_planes(c, trans, unit, true, n, a, lda, X[0], X[1], X[2], L.ldp) != cudaSuccess)
+    // 2.+3. FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
+    //       leaves of 32 and the split levels 32, 64, 128), with their planes
+    (void)scratch;
+    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp) != cudaSuccess)
         return TRI_ERR_CUDA;
 
     auto pl = [&](const __nv_bfloat16 *p, int64_t rows, int64_t cols, int64_t ld) {
