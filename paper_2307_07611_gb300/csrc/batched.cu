@@ -113,10 +113,38 @@ __device__ __forceinline__ int warp_tile_inverse(T *t, int lane, int valid) {
 // diagonal block starting at row row0 of a larger matrix (pivot errors report the row,
 // and the BF16 hi/mid/lo planes of the whole block are written when p0 != nullptr);
 // row0 < 0: a block of a batch (pivot errors report d.index).
+// Writes the BF16 hi/mid/lo planes of the whole (nt*32)^2 block held in the tiles (the
+// strict upper part as zeros) at rows/columns row0 + ... of planes with leading dim ldp.
+template <typename T, int NT>
+__device__ __forceinline__ void write_planes(const T *tiles, int nt, int n, long long row0, long long ntot,
+                                             __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
+                                             long long ldp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarps = NT / 32;
+    for (int e = warp; e < nt * nt; e += nwarps) {
+        const int I = e / nt, J = e % nt;
+        const T *tp = I >= J ? tiles + (size_t)(I * (I + 1) / 2 + J) * TE : nullptr;
+#pragma unroll 4
+        for (int c = 0; c < 32; ++c) {
+            const long long gi = row0 + I * 32 + lane, gj = row0 + J * 32 + c;
+            if (gi >= ntot || gj >= ntot || I * 32 + lane >= n || J * 32 + c >= n) continue;
+            const float v = tp ? (float)tp[lane * TP + c] : 0.f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const float r1 = v - __bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            const long long o = gi + gj * ldp;
+            p0[o] = h;
+            p1[o] = m;
+            p2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        }
+    }
+}
+
 template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
 __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
-                                             long long ldp, long long ntot) {
+                                             long long ldp, long long ntot, __nv_bfloat16 *q0 = nullptr,
+                                             __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = NT / 32;
     const int n = d.n, nt = (n + 31) / 32;
@@ -152,6 +180,12 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
         }
     }
     __syncthreads();
+
+    // Planes of T itself (diagonal blocks of the mixed path), before inverting.
+    if (q0 != nullptr) {
+        write_planes<T, NT>(tiles, nt, n, row0, ntot, q0, q1, q2, ldp);
+        __syncthreads();   // the inversion below overwrites the tiles in place
+    }
 
     // Diagonal tiles.
     for (int I = warp; I < nt; I += nwarps) {
@@ -225,26 +259,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = tp[r * TP + c];
         }
     }
-    if (p0 != nullptr) {
-        // BF16 planes of the whole diagonal block (the strict upper part as zeros).
-        for (int e = warp; e < nt * nt; e += nwarps) {
-            const int I = e / nt, J = e % nt;
-            const T *tp = I >= J ? tile_ptr(tiles, I, J) : nullptr;
-#pragma unroll 4
-            for (int c = 0; c < 32; ++c) {
-                const long long gi = row0 + I * 32 + lane, gj = row0 + J * 32 + c;
-                if (gi >= ntot || gj >= ntot || I * 32 + lane >= n || J * 32 + c >= n) continue;
-                const float v = tp ? (float)tp[lane * TP + c] : 0.f;
-                const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                const float r1 = v - __bfloat162float(h);
-                const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-                const long long o = gi + gj * ldp;
-                p0[o] = h;
-                p1[o] = m;
-                p2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
-            }
-        }
-    }
+    if (p0 != nullptr) write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
 }
 
 template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
@@ -271,13 +286,14 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict_
 template <bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long lda, long long n, long long *info,
                                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1,
-                                                             __nv_bfloat16 *p2, long long ldp) {
+                                                             __nv_bfloat16 *p2, long long ldp, __nv_bfloat16 *q0,
+                                                             __nv_bfloat16 *q1, __nv_bfloat16 *q2) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
     float *wt = tiles + (size_t)BLimits<8>::kTiles * TE;
     const long long r0 = (long long)blockIdx.x * 256;
     BDesc d{a + vidx<TRANS>(r0, r0, lda), lda, (int)min(256ll, n - r0), (int)blockIdx.x};
-    invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n);
+    invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n, q0, q1, q2);
 }
 
 template <typename T, int MAXT>
@@ -306,9 +322,11 @@ KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *sme
 }  // namespace
 
 // Inverts the 256 x 256 diagonal blocks of an n x n FP32 matrix in place (one CTA each)
-// and writes their BF16 planes (used by the mixed path).
+// and writes the BF16 planes of the inverse blocks (p*) and, if q0 != nullptr, of the
+// original blocks (q*) (used by the mixed path).
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
-                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp) {
+                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
+                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2) {
     const int64_t blocks = (n + 255) / 256;
     if (blocks <= 0) return cudaSuccess;
     const size_t smem = smem_bytes<float, 8>();
@@ -322,7 +340,7 @@ cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, f
         fl += nb * nb * nb / 3.0;
     }
     TraceScope ts(c.stream, "diag_blocks", fl, (double)n * 256.0 * (4.0 + 4.0 + 6.0));
-    k<<<(unsigned)blocks, 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp);
+    k<<<(unsigned)blocks, 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp, q0, q1, q2);
     return cudaGetLastError();
 }
 

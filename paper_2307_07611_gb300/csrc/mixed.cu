@@ -29,9 +29,32 @@ namespace triinv {
 
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
-                                __nv_bfloat16 *p2, int64_t ldp);
+                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag);
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
-                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp);
+                               __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
+                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2);
+
+// Per-device side stream and events used to run two independent kernels concurrently
+// (fork / join through events, so the pair also works inside stream capture).
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+SideStream g_side[64];
+
+// Caller holds g_side_mu for the whole fork / launch / join sequence, so concurrent
+// calls from several host threads never interleave their event records.
+bool side_stream(int dev, SideStream **out) {
+    SideStream &ss = g_side[dev];
+    if (!ss.s) {
+        if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) != cudaSuccess) return false;
+    }
+    *out = &ss;
+    return true;
+}
 
 namespace {
 
@@ -198,14 +221,25 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     tri_status st = build_plan(c.device, c.sm_count, n, &plan);
     if (st != TRI_OK) return st;
 
-    // 1. T planes
-    if (launch_split_planes(c, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp) != cudaSuccess)
-        return TRI_ERR_CUDA;
-    // 2.+3. FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
-    //       leaves of 32 and the split levels 32, 64, 128), with their planes
+    // 1. T planes of the off-diagonal part (side stream), concurrently with
+    // 2.+3. the FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
+    //       leaves of 32 and the split levels 32, 64, 128), which also writes the T and X
+    //       planes of its block.  The two touch disjoint parts of T.
     (void)scratch;
-    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp) != cudaSuccess)
+    SideStream *ss = nullptr;
+    std::unique_lock<std::mutex> side_lock(g_side_mu);
+    if (!side_stream(c.device, &ss)) return TRI_ERR_CUDA;
+    if (cudaEventRecord(ss->fork, c.stream) != cudaSuccess || cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
+    Ctx cs = c;
+    cs.stream = ss->s;
+    if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true) != cudaSuccess)
+        return TRI_ERR_CUDA;
+    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2]) != cudaSuccess)
+        return TRI_ERR_CUDA;
+    if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
+        return TRI_ERR_CUDA;
+    side_lock.unlock();
 
     auto pl = [&](const __nv_bfloat16 *p, int64_t rows, int64_t cols, int64_t ld) {
         return tc::Plane{p, rows, cols, ld};

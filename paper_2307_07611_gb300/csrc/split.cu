@@ -34,7 +34,8 @@ template <bool TRANS, bool UNIT, bool DIAG_ONLY>
 __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a, int64_t lda, int64_t n,
                                                     __nv_bfloat16 *__restrict__ p0,
                                                     __nv_bfloat16 *__restrict__ p1,
-                                                    __nv_bfloat16 *__restrict__ p2, int64_t ldp) {
+                                                    __nv_bfloat16 *__restrict__ p2, int64_t ldp,
+                                                    bool skip_diag) {
     int64_t i0, j0;
     if (DIAG_ONLY) {
         i0 = (int64_t)blockIdx.z * 256 + blockIdx.x * TS;
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
         j0 = (int64_t)blockIdx.y * TS;
         const bool diag_block = (i0 / 256) == (j0 / 256);
         if (!diag_block && j0 > i0) return;        // strictly upper block: never read
+        if (diag_block && skip_diag) return;       // written by the diagonal-block kernel
     }
     if (i0 >= n || j0 >= n) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -157,13 +159,13 @@ cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t
 
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
-                                __nv_bfloat16 *p2, int64_t ldp) {
+                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag) {
     const int64_t t = (n + TS - 1) / TS;
     if (t <= 0) return cudaSuccess;
     dim3 grid = diag_only ? dim3(256 / TS, 256 / TS, (unsigned)((n + 255) / 256)) : dim3((unsigned)t, (unsigned)t);
     const double elems = diag_only ? (double)n * 256.0 : (double)n * n / 2.0;
     TraceScope ts(c.stream, diag_only ? "split_diag" : "split_t", 0.0, elems * (4.0 + 6.0));
-#define TRI_SPLIT(TR, UN, DO) split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp)
+#define TRI_SPLIT(TR, UN, DO) split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp, skip_diag)
     if (diag_only) {
         if (trans) { if (unit) TRI_SPLIT(true, true, true); else TRI_SPLIT(true, false, true); }
         else { if (unit) TRI_SPLIT(false, true, true); else TRI_SPLIT(false, false, true); }
