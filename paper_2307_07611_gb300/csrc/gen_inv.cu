@@ -9,7 +9,8 @@
 //     (K22, S22) = rec(A22)
 //     K21 = -K22 (L21 K11),   S12 = -(S11 U12) S22               (block inverses, Section 3)
 // and finally A^-1 = S K (upper times unit lower).  Leaves (128 x 128 in FP32, 64 x 64 in
-// FP64) are factored and inverted by one CTA in shared memory.  Flops: LU 2n^3/3, inverse
+// FP64) are factored by one CTA in shared memory, and their L and U are inverted there by
+// the tiled split of tile_inverse.cuh.  Flops: LU 2n^3/3, inverse
 // factors 2n^3/3, product 2n^3/3.
 //
 // K (strict lower, unit diagonal implied) and S (upper with diagonal) share one n x n
@@ -20,53 +21,27 @@
 #include <vector>
 
 #include "gemm.cuh"
+#include "tile_inverse.cuh"
 
 namespace triinv {
 namespace {
 
-// Right-looking column recurrence on a lower view held in shared memory (the same sums as
-// the CRIT recurrence, Section 4.2): each thread keeps rows ig + r*G of column j of the
-// inverse in registers; one barrier per k.  get(i, k) reads the lower view.
-template <typename T, int L, int NT, bool UNIT, typename Get>
-__device__ __forceinline__ void lower_inverse_regs(Get get, int nb, T (&acc)[L * L / NT], T (*xrow)[L]) {
-    constexpr int G = NT / L;
-    constexpr int RPT = L * L / NT;
-    const int j = threadIdx.x % L, ig = threadIdx.x / L;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) acc[r] = T(0);
-    for (int k = 0; k < nb; ++k) {
-        const T dk = UNIT ? T(1) : T(1) / get(k, k);
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int i = ig + r * G;
-            if (i == k && j <= k) {
-                const T x = (j == k) ? dk : -acc[r] * dk;
-                acc[r] = x;
-                xrow[k & 1][j] = x;
-            }
-        }
-        __syncthreads();
-        if (j <= k) {
-            const T xkj = xrow[k & 1][j];
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int i = ig + r * G;
-                if (i > k && i < nb) acc[r] = fma(get(i, k), xkj, acc[r]);
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// One leaf block [off, off + nb) of A: unpivoted LU in shared memory, then
-// K = L^-1 (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
+// One leaf block [off, off + nb) of A (nb <= L): unpivoted Doolittle LU in shared memory,
+// then K = L^-1 (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
+// The two triangular inverses run on the tiled in-shared-memory split (tile_inverse.cuh):
+// L (unit diagonal) and U^T are copied into 32 x 32 tiles and inverted there.
 template <typename T, int L, int NT>
 __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *__restrict__ a, int64_t lda, T *__restrict__ ks,
                                                      int64_t ldk, int64_t off, int nb, long long *info) {
+    constexpr int NTL = L / 32;                         // tile rows
+    constexpr int KT = NTL * (NTL + 1) / 2;             // lower tiles
+    constexpr int WT = (NTL / 2) * (NTL / 2) > 0 ? (NTL / 2) * (NTL / 2) : 1;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T (*s)[L + 1] = reinterpret_cast<T (*)[L + 1]>(smem_raw);
-    T (*xrow)[L] = reinterpret_cast<T (*)[L]>(smem_raw + sizeof(T) * L * (L + 1));
-    const int tid = threadIdx.x;
+    T *tiles = reinterpret_cast<T *>(smem_raw + sizeof(T) * L * (L + 1));
+    T *wt = tiles + (size_t)KT * TE;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
     for (int idx = tid; idx < L * L; idx += NT) {
         const int i = idx % L, j = idx / L;
         T v = (i == j) ? T(1) : T(0);
@@ -74,38 +49,120 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *__restrict__ a, in
         s[i][j] = v;
     }
     __syncthreads();
-    // Doolittle LU, right-looking: column k of L, then the rank-1 Schur update.
-    for (int k = 0; k < nb; ++k) {
-        const T piv = s[k][k];
-        if (tid == 0 && (piv == T(0) || !isfinite(piv))) atomicMin(info, (long long)(off + k));
-        const T rp = T(1) / piv;
-        for (int i = k + 1 + tid; i < nb; i += NT) s[i][k] *= rp;
+    // Doolittle LU, right-looking, on register blocks: thread t owns rows 8*(t % RG) + r
+    // (r < 8) and columns CW*(t / RG) + c (c < CW) of the block.  Step k broadcasts row k
+    // (u_kj) and the scaled column k (l_ik) through shared memory (double-buffered by the
+    // parity of k), then every thread updates its block: a_ij -= l_ik u_kj.
+    {
+        constexpr int RG = L / 8;                       // row groups
+        constexpr int CW = L * L / (NT * 8);            // columns per thread
+        static_assert(RG * (NT / RG) == NT && CW * (NT / RG) == L, "LU register layout");
+        T *rowk = tiles;                                // 2 x L scratch (tiles are free here)
+        T *colk = tiles + 2 * L;
+        const int rg = tid % RG, cg = tid / RG;
+        T v[8][CW];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) v[r][c] = s[rg * 8 + r][cg * CW + c];
         __syncthreads();
-        // Rank-1 update on a (NT/32) x 32 thread grid: rows step by NT/32, columns by 32.
-        for (int j = k + 1 + (tid >> 5); j < nb; j += NT / 32) {
-            const T ukj = s[k][j];
-            for (int i = k + 1 + (tid & 31); i < nb; i += 32) s[i][j] = fma(-s[i][k], ukj, s[i][j]);
+        for (int k = 0; k < nb; ++k) {
+            T *rk = rowk + (k & 1) * L;
+            T *ck = colk + (k & 1) * L;
+            if (rg == (k >> 3)) {
+                const int kr = k & 7;
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    T val = v[0][c];
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) val = (r == kr) ? v[r][c] : val;
+                    rk[cg * CW + c] = val;
+                }
+            }
+            __syncthreads();
+            const T piv = rk[k];
+            if (tid == 0 && (piv == T(0) || !isfinite(piv))) atomicMin(info, (long long)(off + k));
+            const T rp = T(1) / piv;
+            if (cg == k / CW) {
+                const int kc = k % CW;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = rg * 8 + r;
+                    T val = v[r][0];
+#pragma unroll
+                    for (int c = 1; c < CW; ++c) val = (c == kc) ? v[r][c] : val;
+                    const T l = val * rp;
+                    if (i > k) ck[i] = l;
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) v[r][c] = (c == kc && i > k) ? l : v[r][c];
+                }
+            }
+            __syncthreads();
+            T lr[8], uc[CW];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) lr[r] = ck[rg * 8 + r];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) uc[c] = rk[cg * CW + c];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    const int i = rg * 8 + r, j = cg * CW + c;
+                    if (i > k && j > k) v[r][c] = fma(-lr[r], uc[c], v[r][c]);
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) s[rg * 8 + r][cg * CW + c] = v[r][c];
+        __syncthreads();
+    }
+    const int nt = (nb + 31) / 32;
+    for (int pass = 0; pass < 2; ++pass) {
+        // pass 0: lower view = L (unit diagonal); pass 1: lower view = U^T.
+        for (int tl = warp; tl < nt * (nt + 1) / 2; tl += nwarps) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+            const int J = tl - I * (I + 1) / 2;
+            T *tp = tile_ptr(tiles, I, J);
+            for (int c = 0; c < 32; ++c) {
+                const int i = I * 32 + lane, j = J * 32 + c;
+                T v;
+                if (i >= nb || j >= nb) v = (i == j) ? T(1) : T(0);
+                else if (j > i) v = T(0);
+                else if (j == i) v = pass == 0 ? T(1) : s[i][i];
+                else v = pass == 0 ? s[i][j] : s[j][i];
+                tp[lane * TP + c] = v;
+            }
+        }
+        __syncthreads();
+        invert_tiles<T, NT>(tiles, wt, nt, nb);
+        for (int tl = warp; tl < nt * (nt + 1) / 2; tl += nwarps) {
+            int I = 0;
+            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+            const int J = tl - I * (I + 1) / 2;
+            const T *tp = tile_ptr(tiles, I, J);
+            for (int c = 0; c < 32; ++c) {
+                const int i = I * 32 + lane, j = J * 32 + c;
+                if (i >= nb || j >= nb || j > i) continue;
+                if (pass == 0) {
+                    if (j < i) ks[(off + i) + (off + j) * ldk] = tp[lane * TP + c];   // K, strict lower
+                } else {
+                    ks[(off + j) + (off + i) * ldk] = tp[lane * TP + c];              // S = (U^T)^-1 ^T
+                }
+            }
         }
         __syncthreads();
     }
-    constexpr int RPT = L * L / NT;
-    constexpr int G = NT / L;
-    const int j = tid % L, ig = tid / L;
-    T acc[RPT];
-    // K = L^-1: lower view of the strict lower part with a unit diagonal.
-    lower_inverse_regs<T, L, NT, true>([&](int i, int k) { return s[i][k]; }, nb, acc, xrow);
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int i = ig + r * G;
-        if (i < nb && j < i) ks[(off + i) + (off + j) * ldk] = acc[r];
-    }
-    // S = U^-1 = ((U^T)^-1)^T: lower view U^T(i, k) = s[k][i].
-    lower_inverse_regs<T, L, NT, false>([&](int i, int k) { return s[k][i]; }, nb, acc, xrow);
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-        const int i = ig + r * G;
-        if (i < nb && j <= i) ks[(off + j) + (off + i) * ldk] = acc[r];
-    }
+}
+
+template <typename T, int L>
+constexpr size_t lu_leaf_smem() {
+    constexpr int NTL = L / 32;
+    constexpr int KT = NTL * (NTL + 1) / 2;
+    constexpr int WT = (NTL / 2) * (NTL / 2) > 0 ? (NTL / 2) * (NTL / 2) : 1;
+    return sizeof(T) * ((size_t)L * (L + 1) + (size_t)(KT + WT) * TE);
 }
 
 struct Node {
@@ -186,12 +243,15 @@ cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int6
                   (double)nb * nb * nb * 4.0 / 3.0, 0.0);
     if (g.dt == TRI_F64) {
         constexpr int L = 64, NT = 256;
-        const size_t sm = sizeof(double) * (L * (L + 1) + 2 * L);
+        constexpr size_t sm = lu_leaf_smem<double, L>();
+        cudaError_t e = cudaFuncSetAttribute(lu_leaf_kernel<double, L, NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
         lu_leaf_kernel<double, L, NT><<<1, NT, sm, g.c->stream>>>((const double *)a, lda, (double *)ks, ldk,
                                                                   off, nb, g.c->info);
     } else {
-        constexpr int L = 128, NT = 1024;
-        const size_t sm = sizeof(float) * (L * (L + 1) + 2 * L);
+        constexpr int L = 128, NT = 512;
+        constexpr size_t sm = lu_leaf_smem<float, L>();
         cudaError_t e = cudaFuncSetAttribute(lu_leaf_kernel<float, L, NT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
