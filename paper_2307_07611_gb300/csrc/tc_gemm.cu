@@ -347,7 +347,13 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int t_begin = cta_off[blockIdx.x], t_end = cta_off[blockIdx.x + 1];
+    const int t_begin = cta_off[blockIdx.x], t_end = cta_off[blockIdx.x + 1];   // plan data: constant
+    // Programmatic dependent launch: the set-up above may overlap the previous kernel on
+    // the stream; no global data it produces (or reads) is touched before this wait.  The
+    // trigger lets the next kernel's CTAs start their own set-up as SMs free up; it can
+    // only take effect once every CTA of this grid has started.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
@@ -569,8 +575,17 @@ cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const T
         if (e != cudaSuccess) return e;
         attr_set[c.device] = true;
     }
-    kern<<<ctas, NTHREADS, SMEM_BYTES, c.stream>>>(maps, terms, d_tiles, d_off, epi, c.timeout);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, maps, terms, d_tiles, d_off, epi, c.timeout);
 }
 
 }  // namespace
