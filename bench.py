@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--no-quality", action="store_true",
                    help="skip the residual / oracle check (for profiler launch lists)")
     p.add_argument("--cpu-sample-stride", type=int, default=1)
+    p.add_argument("--profile-config", default=None,
+                   choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512"],
+                   help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
     return p.parse_args()
@@ -53,6 +56,24 @@ def parse():
 
 def flops_tri(n: int) -> float:
     return n ** 3 / 3.0
+
+
+def dominant_traffic(kernel: str):
+    """Per-launch DRAM bytes (read + write) of `kernel` from the committed ncu summary,
+    or None if there is none or the kernel source changed since it was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_n8192.json")
+    src = os.path.join(ROOT, "paper_2307_07611_gb300", "csrc", f"{kernel}.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("source_sha256") != digest:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
 
 
 def load_peaks():
@@ -190,25 +211,31 @@ def event_time(torch, fn, reps, warmup=1, setup=None):
     return statistics.median(ms)
 
 
-def secondary(torch, lib, dev):
+def secondary(torch, lib, dev, only=None):
     import numpy as np
     from paper_2307_07611_gb300 import inputs
     out = {}
     sh = int(torch.cuda.current_stream().cuda_stream)
+    want = lambda name: only is None or only == name
 
     # single lower FP64 n = 512 (uniform law, seed 0), plain recursion, leaf 64
     n = 512
-    t = inputs.tri_lower(n, seed=0, law="uniform")
-    pr = torch.from_numpy(np.ascontiguousarray(t.T)).to(dev)
-    wk = torch.empty_like(pr)
-    ms = event_time(torch, lambda: lib.check(lib.tri_inv(0, 0, n, wk.data_ptr(), n, lib.TRI_F64, sh)), 20, 3,
-                    setup=lambda: wk.copy_(pr))
-    xd = wk.T.tril()
-    td = pr.T.tril()
-    r = td @ xd
-    r.diagonal().sub_(1.0)
-    out["single_f64_n512"] = {"value": n ** 3 / 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (n^3/3)", "ms": ms,
-                              "residual": float(r.norm() / (td.norm() * xd.norm()))}
+    if not want("single_f64_n512"):
+        n = 0
+    if n:
+        t = inputs.tri_lower(n, seed=0, law="uniform")
+        pr = torch.from_numpy(np.ascontiguousarray(t.T)).to(dev)
+        wk = torch.empty_like(pr)
+        ms = event_time(torch, lambda: lib.check(lib.tri_inv(0, 0, n, wk.data_ptr(), n, lib.TRI_F64, sh)), 20, 3,
+                        setup=lambda: wk.copy_(pr))
+        xd = wk.T.tril()
+        td = pr.T.tril()
+        r = td @ xd
+        r.diagonal().sub_(1.0)
+        out["single_f64_n512"] = {"value": n ** 3 / 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (n^3/3)", "ms": ms,
+                                  "residual": float(r.norm() / (td.norm() * xd.norm()))}
+    if only is not None and not want("general_f32_n16384"):
+        return _secondary_rest(torch, lib, dev, out, only)
 
     # general dense FP32 n = 16384: A = N(0,1)/sqrt(n) + 2I, block LU then U^-1 L^-1
     n = 16384
@@ -234,6 +261,16 @@ def secondary(torch, lib, dev):
         del ws
     out["general_f32_n16384"] = res
     del pr, wk
+    return _secondary_rest(torch, lib, dev, out, only)
+
+
+def _secondary_rest(torch, lib, dev, out, only):
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    want = lambda name: only is None or only == name
+    if not want("batched_4096"):
+        return _secondary_adjoint(torch, lib, dev, out, only)
 
     # batched: 4096 lower FP32 blocks, sizes U{16..256}, one persistent graph-captured launch
     sizes, blocks = inputs.batched_blocks(4096, seed=0, dtype=np.float32)
@@ -251,6 +288,15 @@ def secondary(torch, lib, dev):
                            "dense_bytes_GBps": 2 * host.nbytes / (ms * 1e-3) / 1e9}
     lib.tri_batched_plan_destroy(plan)
     del pr, wk
+    return _secondary_adjoint(torch, lib, dev, out, only)
+
+
+def _secondary_adjoint(torch, lib, dev, out, only):
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    if only is not None and only != "adjoint_256x1024":
+        return out
 
     # differentiation: batch 256 of n = 1024 FP32 lower (uniform law), loss sum(W * T^-1)
     b, n = 256, 1024
@@ -280,6 +326,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_config:
+        import torch
+        from paper_2307_07611_gb300 import lib
+        lib.load()
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        torch.cuda.set_device(dev)
+        print(json.dumps({"profile_config": args.profile_config,
+                          "result": secondary(torch, lib, dev, only=args.profile_config)}), flush=True)
+        return 0
 
     import numpy as np
     import torch
@@ -423,7 +478,7 @@ def main():
             peak = props.multi_processor_count * fma_per_clk * 2 * mhz * 1e6 / 1e12
             src = f"derived: {props.multi_processor_count} SMs x {fma_per_clk} FMA/clk x 2 x {mhz:.0f} MHz"
         roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "frac": achieved / peak, "traffic": dominant_traffic(name), "peak_source": src,
                 "launches": rec["launches"], "avg_launch_ms": rec["ms"] / rec["launches"],
                 "share_of_step": rec["ms"] / traced_ms, "traced_ms_per_step": traced_ms / args.steps}
     launches = sum(v["launches"] for v in trace.values()) if trace else None
