@@ -466,7 +466,7 @@ def main():
                 g[k] += rec[k]
         name, rec = max(groups.items(), key=lambda kv: kv[1]["ms"])
         achieved = rec["flops"] / (rec["ms"] * 1e-3) / 1e12
-        if name.startswith("tc_gemm"):
+        if name.startswith("tc_"):
             bound, unit = "tensor", "TFLOP/s"
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             src = f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"

@@ -239,6 +239,21 @@ TRI_API tri_status tri_tc_gemm_bf16(int64_t m, int64_t n, int64_t k, int nterms,
                                     const void *const *b_planes, int64_t ldb, float *c,
                                     int64_t ldc, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * tri_mixed_schedule_stats -- host-only inspection of the TRI_F32_MIXED schedule for
+ * order n on `ctas` persistent CTAs (no device call).  The mixed path runs the products
+ * of every split level (block inverse of the proof of the main Theorem, Section 3:
+ * W = B X_A, X21 = -X_C W) and of the Newton-Schulz step (R = I - T X, X += X R) as one
+ * launch over a DAG of 128 x 256 output tiles, list-scheduled longest path first.
+ * Writes into the host array stats[0..7]: number of tiles, dependency edges, modelled
+ * makespan, longest dependency path and total work / ctas (the last three in pipeline
+ * slots of one 128 x 256 x 64 product), 1.0 if the per-CTA lists replay to completion
+ * (no circular wait), algorithmic flops, CTAs used.
+ * Errors: TRI_ERR_ARG for n <= 256 (no tensor-core part), ctas < 1, nstats < 8 or a NULL
+ * stats; TRI_ERR_UNSUPPORTED for n > 2^20.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_mixed_schedule_stats(int64_t n, int ctas, double *stats, int nstats);
+
 /* Synchronises `stream`, then reports and clears the device-side status of the calling
  * thread's current device: TRI_ERR_SINGULAR with *first_bad_index set to the smallest
  * bad pivot index recorded since the last call, TRI_ERR_TIMEOUT if a bounded wait ran
@@ -258,6 +273,16 @@ TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
  * --------------------------------------------------------------------------------- */
 TRI_API void tri_trace_enable(int on);
 TRI_API int64_t tri_trace_report(char *buf, size_t cap);
+
+/* Per-tile device timeline of the last TRI_F32_MIXED tensor-core launch made while tracing
+ * was enabled.  Synchronises the device, then copies up to cap_words 64-bit words into the
+ * host buffer `buf` (6 words per tile, in each CTA's processing order): [0] = CTA | op << 16
+ * | k-blocks << 20 | (row tile) << 32 | (column tile) << 48 with op 0 = W = B X_A,
+ * 1 = X21 = -X_C W, 2 = R = I - T X, 3 = X += X R; [1] producer starts waiting for the
+ * tile's input regions; [2] first operand load issued; [3] MMA issuer starts the tile;
+ * [4] last MMA issued; [5] epilogue done (GPU global timer, ns).  Returns the number of
+ * tiles, 0 if no such launch was traced, -1 on a CUDA error.  buf may be NULL. */
+TRI_API int64_t tri_trace_timeline(unsigned long long *buf, size_t cap_words);
 
 #ifdef __cplusplus
 }

@@ -108,6 +108,11 @@ void clear_trace_locked() {
 
 }  // namespace
 
+bool trace_on() {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    return g_trace_on;
+}
+
 TraceScope::TraceScope(cudaStream_t stream, const char *kernel, double flops, double bytes)
     : slot(-1), stream_(stream) {
     std::lock_guard<std::mutex> lk(g_trace_mu);

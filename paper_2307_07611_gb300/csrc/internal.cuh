@@ -33,6 +33,9 @@ tri_status device_ctx_public(cudaStream_t stream, Ctx *out);
 // ---- tracing (api.cu) -------------------------------------------------------------
 // While tracing is on, TraceScope records a CUDA event pair around the launches made in
 // its lifetime on `stream`, and books the launch's algorithmic flops and bytes.
+// True while kernel tracing is enabled (tri_trace_enable).
+bool trace_on();
+
 struct TraceScope {
     int slot;
     TraceScope(cudaStream_t stream, const char *kernel, double flops, double bytes);

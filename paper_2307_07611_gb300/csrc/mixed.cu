@@ -16,14 +16,18 @@
 //        X += X R          1 term: R is as small as the forward residual (~3e-8
 //                          normwise at n = 8192), so the BF16 error 2^-8 |X R| of the
 //                          update adds ~1e-10, far below FP32 rounding
-// The tile lists of every product depend on n only and are built once per (device, n)
-// and kept in device memory.
+// Steps 4 and 5 run either as one persistent tensor-core launch per product (default)
+// or as a single launch that follows the data dependencies tile by tile (tc_graph.cu,
+// TRI_MIXED_SCHEDULE=graph).  Tile lists and schedules depend on n only and are built
+// once per (device, n).
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <vector>
 
-#include "tc_gemm.cuh"
+#include "tc_graph.cuh"
 
 namespace triinv {
 
@@ -66,26 +70,22 @@ int64_t cdiv(int64_t x, int64_t m) { return (x + m - 1) / m; }
 
 struct Layout {
     int64_t ldp;
-    size_t off_t, off_x, off_r, off_w, off_s, total;
-    int64_t wmax;    // elements of one W plane (largest level)
+    size_t off_t, off_x, off_r, off_w, off_f, total;
 };
 
+// Workspace: T planes (3), X planes (3), R plane, W planes (2, at the positions of the
+// B blocks of T), then the ready counters of the tensor-core launch.
 Layout layout(int64_t n) {
     Layout L{};
     L.ldp = round_up(std::max<int64_t>(n, 1), 64);
-    const size_t plane = (size_t)L.ldp * (size_t)n * 2;
-    L.wmax = 0;
-    for (int64_t h = kDiag; h < n; h *= 2) L.wmax = std::max(L.wmax, level_pairs(n, h) * h * h);
-    size_t sbytes = 0;
-    for (int64_t h = kLeaf; h < std::min(n, kDiag); h *= 2)
-        sbytes = std::max(sbytes, (size_t)(level_pairs(n, h) * h * h) * 4);
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t plane = al((size_t)L.ldp * (size_t)n * 2);
     L.off_t = 0;
-    L.off_x = L.off_t + 3 * al(plane);
-    L.off_r = L.off_x + 3 * al(plane);
-    L.off_w = L.off_r + al(plane);
-    L.off_s = L.off_w + 2 * al((size_t)L.wmax * 2);
-    L.total = L.off_s + al(sbytes);
+    L.off_x = L.off_t + 3 * plane;
+    L.off_r = L.off_x + 3 * plane;
+    L.off_w = L.off_r + plane;
+    L.off_f = L.off_w + 2 * plane;
+    L.total = L.off_f + al(tc::graph_flag_bytes(n));
     return L;
 }
 
@@ -100,6 +100,18 @@ struct Plan {
     std::vector<Launch> w, x21;   // per tc level
     Launch res{}, upd{};
 };
+
+// Schedule of the tensor-core products: "levels" (default) launches one persistent kernel
+// per product (W and X21 per level, R, the update); "graph" runs them all in one launch
+// that follows the tile dependencies (tc_graph.cu).  Chosen once per process from the
+// environment variable TRI_MIXED_SCHEDULE.
+bool use_graph_schedule() {
+    static const bool g = [] {
+        const char *e = std::getenv("TRI_MIXED_SCHEDULE");
+        return e && std::strcmp(e, "graph") == 0;
+    }();
+    return g;
+}
 
 std::mutex g_plan_mu;
 std::map<std::pair<int, int64_t>, Plan> g_plans;
@@ -212,20 +224,19 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         X[i] = (__nv_bfloat16 *)(base + L.off_x + i * plane);
     }
     R[0] = (__nv_bfloat16 *)(base + L.off_r);
-    const size_t wplane = ((size_t)L.wmax * 2 + 255) / 256 * 256;
     W[0] = (__nv_bfloat16 *)(base + L.off_w);
-    W[1] = (__nv_bfloat16 *)(base + L.off_w + wplane);
-    void *scratch = base + L.off_s;
+    W[1] = (__nv_bfloat16 *)(base + L.off_w + plane);
 
+    const bool graph = use_graph_schedule();
+    const tc::GraphPlan *gplan = nullptr;
     Plan *plan = nullptr;
-    tri_status st = build_plan(c.device, c.sm_count, n, &plan);
+    tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan) : build_plan(c.device, c.sm_count, n, &plan);
     if (st != TRI_OK) return st;
 
     // 1. T planes of the off-diagonal part (side stream), concurrently with
     // 2.+3. the FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
     //       leaves of 32 and the split levels 32, 64, 128), which also writes the T and X
     //       planes of its block.  The two touch disjoint parts of T.
-    (void)scratch;
     SideStream *ss = nullptr;
     std::unique_lock<std::mutex> side_lock(g_side_mu);
     if (!side_stream(c.device, &ss)) return TRI_ERR_CUDA;
@@ -241,6 +252,13 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         return TRI_ERR_CUDA;
     side_lock.unlock();
 
+    if (graph) {
+        // 4. + 5. as one dependency-driven launch (W planes at the B-block positions)
+        int *flags = (int *)(base + L.off_f);
+        tc::GEpi ep{a, lda, X[0], X[1], X[2], W[0], W[1], R[0], L.ldp, n, flags,
+                    flags + 3 * gplan->nrb * gplan->ncb, nullptr};
+        return tc::launch_graph(c, trans, unit, n, *gplan, T, ep) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+    }
     auto pl = [&](const __nv_bfloat16 *p, int64_t rows, int64_t cols, int64_t ld) {
         return tc::Plane{p, rows, cols, ld};
     };

@@ -65,8 +65,10 @@ def _declare(lib):
         "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
                               vp, i64, vp], i32),
+        "tri_mixed_schedule_stats": ([i64, i32, ctypes.POINTER(ctypes.c_double), i32], i32),
         "tri_trace_enable": ([i32], None),
         "tri_trace_report": ([ctypes.c_char_p, sz], i64),
+        "tri_trace_timeline": ([ctypes.POINTER(ctypes.c_uint64), sz], i64),
     }
     for name, (args, res) in sigs.items():
         if hasattr(lib, name):
@@ -209,6 +211,17 @@ def tri_tc_gemm_bf16(m, n, k, a_ptrs, lda, b_ptrs, ldb, c, ldc, stream=0) -> int
     return load().tri_tc_gemm_bf16(m, n, k, nt, arr_a, lda, arr_b, ldb, c, ldc, stream or None)
 
 
+def tri_mixed_schedule_stats(n, ctas) -> dict:
+    """Host-only statistics of the mixed path's tensor-core schedule for order n on
+    `ctas` CTAs (no GPU needed).  Raises TriError on bad arguments."""
+    out = (ctypes.c_double * 8)()
+    st = load().tri_mixed_schedule_stats(n, ctas, out, 8)
+    if st != TRI_OK:
+        raise TriError(st, "tri_mixed_schedule_stats")
+    keys = ["tiles", "edges", "makespan", "critical_path", "work_per_cta", "replay_ok", "flops", "ctas"]
+    return dict(zip(keys, list(out)))
+
+
 def tri_get_info(stream=0):
     """Returns (status, first_bad_index)."""
     idx = ctypes.c_int64(-1)
@@ -229,6 +242,28 @@ def tri_trace_report() -> dict:
     buf = ctypes.create_string_buffer(int(need) + 1)
     lib.tri_trace_report(buf, len(buf))
     return json.loads(buf.value.decode())
+
+
+def tri_trace_timeline():
+    """Per-tile timeline of the last traced mixed-path tensor-core launch as a list of
+    dicts (cta, op, kblocks, row_tile, col_tile, wait, load, mma, mma_end, done in ns),
+    or [] if none was traced."""
+    lib = load()
+    nt = lib.tri_trace_timeline(None, 0)
+    if nt < 0:
+        raise TriError(TRI_ERR_CUDA, "tri_trace_timeline")
+    if nt == 0:
+        return []
+    buf = (ctypes.c_uint64 * (6 * nt))()
+    if lib.tri_trace_timeline(buf, 6 * nt) < 0:
+        raise TriError(TRI_ERR_CUDA, "tri_trace_timeline")
+    out = []
+    for t in range(nt):
+        w = buf[6 * t: 6 * t + 6]
+        out.append({"cta": w[0] & 0xFFFF, "op": (w[0] >> 16) & 0xF, "kblocks": (w[0] >> 20) & 0xFFF,
+                    "row_tile": (w[0] >> 32) & 0xFFFF, "col_tile": (w[0] >> 48) & 0xFFFF,
+                    "wait": w[1], "load": w[2], "mma": w[3], "mma_end": w[4], "done": w[5]})
+    return out
 
 
 def check(status: int, what: str = ""):

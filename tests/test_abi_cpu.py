@@ -83,3 +83,56 @@ def test_plain_workspace_formula(libtri):
             best = max(best, pairs * h * h * es)
             h *= 2
         assert lib.tri_inv_workspace_size(n, dt) == best
+
+
+def _tiles_expected(n):
+    """128 x 256 output tiles of the mixed path's products: per split level h >= 256,
+    W = B X_A (h/256 column tiles x ceil(hc/128) row tiles per pair) and X21 (the same
+    count), then R and the update (one tile per 128 x 256 block meeting the lower
+    triangle)."""
+    cd = lambda a, b: -(-a // b)
+    total = 0
+    h = 256
+    while h < n:
+        q = 0
+        while 2 * q * h + h < n:
+            hc = min(h, n - (2 * q * h + h))
+            total += 2 * (h // 256) * cd(hc, 128)
+            q += 1
+        h *= 2
+    ns = sum(cd(min((tm + 1) * 128, n), 256) for tm in range(cd(n, 128)))
+    return total + 2 * ns
+
+
+@pytest.mark.parametrize("n", [257, 300, 512, 777, 1000, 1024, 2048, 3000, 4096, 8192])
+def test_mixed_schedule_is_complete_and_deadlock_free(libtri, n):
+    """The host schedule of the mixed path: every tile once, lists that replay to
+    completion in order (no circular wait), makespan no shorter than either lower bound,
+    flops = the algorithmic count (3 terms per level product, 6 + 1 for Newton-Schulz)."""
+    s = lib.tri_mixed_schedule_stats(n, 152)
+    assert s["tiles"] == _tiles_expected(n)
+    assert s["replay_ok"] == 1.0
+    assert s["makespan"] >= s["critical_path"] - 1e-9
+    assert s["makespan"] >= s["work_per_cta"] - 1e-9
+    fl = 0.0
+    h = 256
+    while h < n:
+        q = 0
+        while 2 * q * h + h < n:
+            hc = min(h, n - (2 * q * h + h))
+            fl += 3.0 * hc * h * (h + 1) + 3.0 * h * hc * (hc + 1)
+            q += 1
+        h *= 2
+    fl += 7.0 * n * (n + 1) * (n + 2) / 3.0
+    assert s["flops"] == pytest.approx(fl, rel=1e-12)
+    assert s["ctas"] == min(152, s["tiles"])
+
+
+def test_mixed_schedule_small_grids_and_errors(libtri):
+    for ctas in (1, 2, 7):
+        s = lib.tri_mixed_schedule_stats(2048, ctas)
+        assert s["replay_ok"] == 1.0 and s["ctas"] == ctas
+    with pytest.raises(lib.TriError):
+        lib.tri_mixed_schedule_stats(256, 152)      # no tensor-core part
+    with pytest.raises(lib.TriError):
+        lib.tri_mixed_schedule_stats(4096, 0)

@@ -161,3 +161,20 @@ def test_mixed_full_size_n8192(lib):
     xp, _ = run_tri_inv(lib, torch, t, lower=True, dtype="f32", ld_pad=0)
     r_mixed, r_plain = normwise_residual(t, x), normwise_residual(t, xp)
     assert r_mixed <= 5e-6 and r_mixed <= 2.0 * r_plain, (r_mixed, r_plain)
+
+
+def test_mixed_graph_schedule_same_results(lib):
+    """The single-launch dependency-driven schedule (TRI_MIXED_SCHEDULE=graph, read once
+    per process) runs the same products in another order: the parity, uplo / diag and
+    bit-exact tests above must pass under it too (run in a child process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TRI_MIXED_SCHEDULE="graph")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "gpu",
+                        os.path.join(root, "tests", "test_gpu_mixed.py"),
+                        "-k", "lower_parity or uplo_diag or integer_families or singular"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    assert " passed" in r.stdout
