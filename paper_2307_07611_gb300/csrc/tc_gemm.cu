@@ -9,8 +9,10 @@
 //   the Newton-Schulz step X <- X + X (I - T X): R = I - T X (6 terms), X += X R (1 term).
 //
 // Structure (one CTA per SM, persistent over a host-built tile list, longest first):
-//   warp 0      TMA producer: per (k-block, term) one pipeline slot = A tile 128x64
-//               (two 64x64 boxes, MN-major) + B tile 256x64 (K-major), 128-byte swizzle.
+//   warp 0      TMA producer: fills a ring of pipeline stages (geometry per mode, see
+//               cfg_for): per (k-block, term) an A tile 128 x 64 (two 64 x 64 boxes,
+//               MN-major) + a B tile 256 x 64 (K-major), or for R = I - T X per 32-wide
+//               k-step all three A and three B plane tiles at once.
 //   warp 1      allocates 512 TMEM columns (two 128x256 FP32 accumulators), one lane
 //               issues tcgen05.mma (M=128, N=256, K=16) and commits slots / accumulators.
 //   warps 2..9  epilogue: tcgen05.ld of the accumulator (two warps per 32-lane quarter,
@@ -19,11 +21,13 @@
 // Every mbarrier wait is bounded (globaltimer); on timeout the kernel records the status,
 // drains its in-flight copies and products, frees TMEM and returns.
 //
-// Operand layouts in shared memory (canonical tcgen05 layouts, 128-byte swizzle):
-//   A (MN-major): atom = 64 M-elements (128 B) x 8 K-rows; M atoms 8192 B apart (LBO),
-//                 K atoms 1024 B apart (SBO).  One MMA (K = 16) spans two K atoms.
-//   B (K-major):  atom = 8 N-rows x 64 K-elements (128 B); N atoms 1024 B apart (SBO);
-//                 the k-offset inside the 128-byte row advances the start address by 32 B.
+// Operand layouts in shared memory (canonical tcgen05 layouts):
+//   A (MN-major, 128-byte swizzle): atom = 64 M-elements (128 B) x 8 K-rows; the two
+//                 64-row atoms ks * 128 B apart (LBO), K atoms 1024 B apart (SBO).  One MMA
+//                 (K = 16) spans two K atoms (2048 B).
+//   B (K-major, 128- or 64-byte swizzle for ks = 64 / 32): atom = 8 N-rows x ks
+//                 K-elements; N atoms ks * 16 B apart (SBO); the k-offset inside the row
+//                 advances the start address by 32 B per K = 16.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -140,35 +144,92 @@ __device__ __forceinline__ void store_upd16(const Epi &ep, int64_t gm, int64_t g
     }
 }
 
-// Number of k-blocks accumulated in tensor memory before the epilogue adds them into
-// FP32 registers (MODE_RES only).  The tensor-core accumulator truncates each add, so a
-// long accumulation drifts towards zero by up to one unit in the last place per MMA; a
-// 256-wide chunk keeps that drift at the size of IEEE FP32 rounding of the whole sum.
-constexpr int kPromoteBlocks = 4;
+// Pipeline geometry per mode.
+//   ks       k per stage: 64 (B tiles 256 x 64 with 128-byte swizzle) or 32 (256 x 32,
+//            64-byte swizzle).  A tiles are 128 x ks, two 64-row boxes with 128-byte swizzle.
+//   fused    true: a stage holds every distinct plane tile the terms read and the MMA
+//            issuer runs all terms on it (each plane crosses L2 once per k-step); false:
+//            a stage holds the A / B pair of one term (loop: chunk, term, k).
+//   promote  MODE_RES: 64-wide k-blocks accumulated in tensor memory before the epilogue
+//            adds them into FP32 registers.  The accumulator truncates every add, so a
+//            product added after the large hi*hi term loses up to one unit in the last
+//            place of the partial sum; the chunk length bounds that loss.
+// R = I - T X reads 3 + 3 planes for 6 terms: fused 32-wide stages (72 KB, 3 deep) halve
+// its L2 traffic; one-term and three-term products keep 64-wide per-term stages (48 KB,
+// 4 deep), which measured faster for them.
+struct Cfg {
+    int ks;
+    bool fused;
+    int promote;
+};
+__host__ __device__ constexpr Cfg cfg_for(int mode) {
+    return mode == MODE_RES ? Cfg{32, true, 1} : Cfg{64, false, 0};
+}
+
+constexpr int STAGE_BUDGET = 216 * 1024;
+constexpr int MAX_STAGES = 9;
+constexpr int GEMM_SMEM_BYTES = STAGE_BUDGET + 1024 + 512;
+
+// Stage layout of one launch (host-computed from the terms and the mode's geometry).
+struct Pipe {
+    int na, nb;          // A / B tiles per stage
+    int stages;          // ring depth
+    int stage_bytes;     // na * BM * ks * 2 + nb * BN * ks * 2
+};
 
 template <int MODE, bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
-tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
+tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe pipe,
                const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
                int *gtimeout) {
     constexpr bool PROMOTE = (MODE == MODE_RES);
+    constexpr Cfg CF = cfg_for(MODE);
+    constexpr int KS = CF.ks;
+    constexpr int A_TILE = BM * KS * 2, B_TILE = BN * KS * 2;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
-    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * STAGES + 5);
+    const int STAGES = pipe.stages;
+    const uint32_t stage_bytes = (uint32_t)pipe.stage_bytes;
+    uint64_t *bars = (uint64_t *)(smem + STAGE_BUDGET);
+    // bars: full[MAX_STAGES], empty[MAX_STAGES], tfull[2], tempty[2], drain
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * MAX_STAGES + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + a); };
-    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * STAGES + 2 + a); };
-    const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
-    // k-blocks per accumulation chunk: one chunk per tile unless promoting.
-    auto chunk_blocks = [&](const Tile &tl) { return PROMOTE ? kPromoteBlocks : (tl.kb1 - tl.kb0); };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (MAX_STAGES + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * MAX_STAGES + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * MAX_STAGES + 2 + a); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * MAX_STAGES + 4);
+    // 64-wide k-blocks per accumulation chunk: one chunk per tile unless promoting.
+    auto chunk_blocks = [&](const Tile &tl) { return PROMOTE ? CF.promote : (tl.kb1 - tl.kb0); };
+    // One stage: load A tiles ia[0..na) and B tiles ib[0..nb) at k.
+    auto load_stage = [&](uint32_t st, uint32_t bar, const Tile &tl, int k, int ia0, int ib0, int na, int nb) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(na * A_TILE + nb * B_TILE));
+        for (int i = 0; i < na; ++i) {
+            const uint32_t dst = st + (uint32_t)(i * A_TILE);
+#pragma unroll
+            for (int c = 0; c < BM / 64; ++c)
+                tma_load_2d(dst + (uint32_t)(c * KS * 128), &maps.a[ia0 + i], tl.am + 64 * c, tl.ak + k, bar);
+        }
+        for (int i = 0; i < nb; ++i)
+            tma_load_2d(st + (uint32_t)(na * A_TILE + i * B_TILE), &maps.b[ib0 + i], tl.bk + k, tl.bn, bar);
+    };
+    // MMAs of one term on stage tiles sa / sb (KS / 16 steps of K = 16).
+    auto mma_term = [&](uint32_t d, uint32_t sa, uint32_t sb, uint32_t &accumulate) {
+#pragma unroll
+        for (int kk = 0; kk < KS / 16; ++kk) {
+            // A: MN-major, 64-row chunks KS * 128 B apart (LBO), 8-row k groups 1024 B
+            // apart (SBO); a k-step of 16 = 2048 B.  B: K-major, 8-row groups KS * 16 B
+            // apart; a k-step of 16 = 32 B inside the swizzled row.
+            const uint64_t da = smem_desc(sa + kk * 2048, KS * 128, 1024, kSwizzle128);
+            const uint64_t db = smem_desc(sb + kk * 32, 16, KS * 16, KS == 64 ? kSwizzle128 : kSwizzle64);
+            tc_mma(d, da, db, kIdesc, accumulate);
+            accumulate = 1;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -212,32 +273,36 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
-            // Order: chunk, then term from the smallest pieces to hi*hi, then k-block.
-            uint32_t it = 0;
+            // Ring position kept incrementally (slot, phase, address): no division by the
+            // runtime ring depth in the issue loop.
+            uint32_t it = 0, ph = 0, st = smem_u32(smem);
+            int s = 0;
             bool ok = true;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const Tile tl = tiles[t];
                 const int cb = chunk_blocks(tl);
                 for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb) {
                     const int c1 = min(c0 + cb, tl.kb1);
-                    for (int j = terms.n - 1; j >= 0 && ok; --j) {
-                        const CUtensorMap *am = &maps.a[terms.a[j]];
-                        const CUtensorMap *bm = &maps.b[terms.b[j]];
-                        for (int kb = c0; kb < c1; ++kb) {
-                            const int s = it % STAGES;
-                            const uint32_t ph = (it / STAGES) & 1u;
-                            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, gtimeout)) {
-                                ok = false;
-                                break;
+                    // fused: one pass with every plane; else one pass per term (smallest first)
+                    for (int j = CF.fused ? 0 : terms.n - 1; j >= 0 && ok; --j) {
+                        for (int kb = c0; kb < c1 && ok; ++kb) {
+                            for (int hk = 0; hk < BK / KS; ++hk) {
+                                if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, gtimeout)) {
+                                    ok = false;
+                                    break;
+                                }
+                                const int k = kb * BK + hk * KS;
+                                if (CF.fused) load_stage(st, full_bar(s), tl, k, 0, 0, pipe.na, pipe.nb);
+                                else load_stage(st, full_bar(s), tl, k, terms.a[j], terms.b[j], 1, 1);
+                                ++it;
+                                if (++s == STAGES) {
+                                    s = 0;
+                                    ph ^= 1u;
+                                    st = smem_u32(smem);
+                                } else {
+                                    st += stage_bytes;
+                                }
                             }
-                            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                            const uint32_t sb = sa + A_BYTES;
-                            mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
-                            const int k = kb * BK;
-                            tma_load_2d(sa, am, tl.am, tl.ak + k, full_bar(s));
-                            tma_load_2d(sa + A_BYTES / 2, am, tl.am + 64, tl.ak + k, full_bar(s));
-                            tma_load_2d(sb, bm, tl.bk + k, tl.bn, full_bar(s));
-                            ++it;
                         }
                     }
                 }
@@ -251,7 +316,8 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            uint32_t it = 0, lc = 0;
+            uint32_t lc = 0, ph = 0, st = smem_u32(smem);
+            int s = 0;
             bool ok = true, issued = false;
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const Tile tl = tiles[t];
@@ -266,27 +332,32 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
                     tc_fence_after();
                     const uint32_t d = tmem_base + a * (uint32_t)BN;
                     uint32_t accumulate = 0;
-                    for (int j = terms.n - 1; j >= 0 && ok; --j) {
-                        for (int kb = c0; kb < c1; ++kb) {
-                            const int s = it % STAGES;
-                            const uint32_t ph = (it / STAGES) & 1u;
-                            if (!mbar_wait(full_bar(s), ph, abort_flag, gtimeout)) {
-                                ok = false;
-                                break;
+                    for (int jj = CF.fused ? 0 : terms.n - 1; jj >= 0 && ok; --jj) {
+                        for (int kb = c0; kb < c1 && ok; ++kb) {
+                            for (int hk = 0; hk < BK / KS; ++hk) {
+                                if (!mbar_wait(full_bar(s), ph, abort_flag, gtimeout)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc_fence_after();
+                                if (CF.fused) {
+                                    // terms from the smallest pieces to hi * hi
+                                    for (int j = terms.n - 1; j >= 0; --j)
+                                        mma_term(d, st + (uint32_t)(terms.a[j] * A_TILE),
+                                                 st + (uint32_t)(pipe.na * A_TILE + terms.b[j] * B_TILE), accumulate);
+                                } else {
+                                    mma_term(d, st, st + (uint32_t)A_TILE, accumulate);
+                                }
+                                issued = true;
+                                tc_commit(empty_bar(s));
+                                if (++s == STAGES) {
+                                    s = 0;
+                                    ph ^= 1u;
+                                    st = smem_u32(smem);
+                                } else {
+                                    st += stage_bytes;
+                                }
                             }
-                            tc_fence_after();
-                            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                            const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-                            for (int kk = 0; kk < BK / 16; ++kk) {
-                                const uint64_t da = smem_desc(sa + kk * 2048, 8192, 1024);
-                                const uint64_t db = smem_desc(sb + kk * 32, 16, 1024);
-                                tc_mma(d, da, db, kIdesc, accumulate);
-                                accumulate = 1;
-                            }
-                            issued = true;
-                            tc_commit(empty_bar(s));
-                            ++it;
                         }
                     }
                     if (ok) tc_commit(tfull_bar(a));
@@ -390,26 +461,26 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms,
 // ---- host side ------------------------------------------------------------------------
 
 template <int MODE, bool TRANS, bool UNIT>
-cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Tile *d_tiles,
+cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Pipe &pipe, const Tile *d_tiles,
                      const int *d_off, int ctas, const Epi &epi) {
     auto kern = tc_gemm_kernel<MODE, TRANS, UNIT>;
     static bool attr_set[64] = {};
     if (!attr_set[c.device]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set[c.device] = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)ctas);
     cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = GEMM_SMEM_BYTES;
     cfg.stream = c.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, maps, terms, d_tiles, d_off, epi, c.timeout);
+    return cudaLaunchKernelEx(&cfg, kern, maps, terms, pipe, d_tiles, d_off, epi, c.timeout);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -429,9 +500,9 @@ bool get_encode() {
 
 }  // namespace
 
-// 2-D map over a column-major BF16 plane: inner dimension = rows, 128-byte swizzle,
-// box = box_rows x box_cols, zero fill outside [0, rows) x [0, cols).
-bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols) {
+// 2-D map over a column-major BF16 plane: inner dimension = rows, 128-byte (or 64-byte)
+// swizzle, box = box_rows x box_cols, zero fill outside [0, rows) x [0, cols).
+bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols, bool swizzle64) {
     if (!get_encode()) return false;
     if (((uintptr_t)p.p & 15) || (p.ld * 2) % 16 || p.rows <= 0 || p.cols <= 0) return false;
     cuuint64_t dims[2] = {(cuuint64_t)p.rows, (cuuint64_t)p.cols};
@@ -439,10 +510,15 @@ bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols) {
     cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)p.p, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
+
+namespace {
+
+}  // namespace
 
 int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int> &offsets) {
     const int nt = (int)tiles.size();
@@ -489,28 +565,40 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
     Maps maps;
     memset(&maps, 0, sizeof(maps));
+    const Cfg cf = cfg_for(mode);
     for (int i = 0; i < 3; ++i) {
         const Plane &pa = aplanes[i < na ? i : 0];
         const Plane &pb = bplanes[i < nb ? i : 0];
-        if (!encode_plane(&maps.a[i], pa, 64, 64)) return cudaErrorInvalidValue;
-        if (!encode_plane(&maps.b[i], pb, 64, BN)) return cudaErrorInvalidValue;
+        if (!encode_plane(&maps.a[i], pa, 64, cf.ks)) return cudaErrorInvalidValue;
+        if (!encode_plane(&maps.b[i], pb, cf.ks, BN, cf.ks == 32)) return cudaErrorInvalidValue;
     }
+    // Stage layout: every distinct plane the terms read (fused), or one term's pair.
+    Pipe pipe{1, 1, 0, 0};
+    for (int j = 0; j < terms.n; ++j) {
+        if (terms.a[j] < 0 || terms.a[j] >= na || terms.b[j] < 0 || terms.b[j] >= nb) return cudaErrorInvalidValue;
+        if (cf.fused) {
+            pipe.na = std::max(pipe.na, terms.a[j] + 1);
+            pipe.nb = std::max(pipe.nb, terms.b[j] + 1);
+        }
+    }
+    pipe.stage_bytes = (pipe.na * BM + pipe.nb * BN) * cf.ks * 2;
+    pipe.stages = std::min(MAX_STAGES, STAGE_BUDGET / pipe.stage_bytes);
     TraceScope ts(c.stream, trace_name, flops, 0.0);
 #define TRI_TC_CASE(M)                                                                   \
     case M:                                                                              \
-        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, d_tiles, d_off, ctas, epi)   \
-                               : launch_t<M, true, false>(c, maps, terms, d_tiles, d_off, ctas, epi); \
-        return unit ? launch_t<M, false, true>(c, maps, terms, d_tiles, d_off, ctas, epi)             \
-                    : launch_t<M, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
+        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)   \
+                               : launch_t<M, true, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi); \
+        return unit ? launch_t<M, false, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)             \
+                    : launch_t<M, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
     switch (mode) {
         TRI_TC_CASE(MODE_W)
         TRI_TC_CASE(MODE_X21)
         TRI_TC_CASE(MODE_RES)
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:
-            return launch_t<MODE_F32, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
+            return launch_t<MODE_F32, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
         case MODE_GEN:
-            return launch_t<MODE_GEN, false, false>(c, maps, terms, d_tiles, d_off, ctas, epi);
+            return launch_t<MODE_GEN, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
         default:
             return cudaErrorInvalidValue;
     }

@@ -57,9 +57,9 @@ struct Plane {
 };
 
 // Encodes a 2-D TMA map over a column-major BF16 plane (inner dimension = rows, 128-byte
-// swizzle, zero fill outside the plane) with box box_rows x box_cols.  False if the
+// or 64-byte swizzle, zero fill outside the plane) with box box_rows x box_cols.  False if the
 // driver entry point is missing or the plane violates the TMA alignment rules.
-bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols);
+bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols, bool swizzle64 = false);
 
 // Greedy longest-processing-time assignment of tiles to `ctas` persistent CTAs: tiles are
 // reordered so that CTA b owns [offsets[b], offsets[b+1]), each list longest first.  The

@@ -116,14 +116,17 @@ static __device__ __forceinline__ void tc_commit(uint32_t bar) {
 }
 
 // Shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4
-// (32-45), version 1 (46-47), base offset 0, swizzle mode 2 = 128-byte (61-63).
-static __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// (32-45), version 1 (46-47), base offset 0, swizzle mode (61-63).
+// Swizzle modes (bits 61-63): 2 = 128-byte, 4 = 64-byte.
+constexpr uint32_t kSwizzle128 = 2, kSwizzle64 = 4;
+static __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                                     uint32_t swizzle = kSwizzle128) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)swizzle << 61;
     return d;
 }
 

@@ -35,9 +35,10 @@ def lib():
 
 
 def colmajor_bf16(x, ld):
-    """x (rows x cols) -> device BF16 tensor, column-major with leading dimension ld."""
+    """x (rows x cols) -> device BF16 tensor, column-major with leading dimension ld; the
+    padding rows hold NaN, which must never reach a stored result."""
     rows, cols = x.shape
-    buf = torch.zeros((cols, ld), dtype=torch.bfloat16)
+    buf = torch.full((cols, ld), float("nan"), dtype=torch.bfloat16)
     buf[:, :rows] = torch.from_numpy(np.ascontiguousarray(x.T)).to(torch.bfloat16)
     return buf.cuda()
 
