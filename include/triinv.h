@@ -157,9 +157,13 @@ TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *co
 
 /* ---------------------------------------------------------------------------------
  * Strided batch of equal-order triangular inverses, in place: matrix b starts at
- * a + b * stride (elements, stride >= lda * n).  TRI_F32 / TRI_F64 run every split level
- * of all matrices in one launch (batch <= 65535); TRI_F32_MIXED inverts them one after
- * another with the mixed path.  Singular pivots record the matrix index.
+ * a + b * stride (elements, stride >= lda * n), batch <= 65535.  TRI_F32 / TRI_F64 run
+ * every split level of all matrices in one launch; TRI_F32_MIXED (n > 256) runs each
+ * product of the mixed path (level products, Newton-Schulz residual and update) as one
+ * tensor-core launch over the tiles of a chunk of matrices whose BF16 planes fit in
+ * 8 GiB (n <= 256: the TRI_F32 levels).  The workspace of the _ex form holds one chunk's
+ * planes (tri_inv_strided_batched_workspace_size).  Singular pivots record the matrix
+ * index.
  * --------------------------------------------------------------------------------- */
 TRI_API tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
                                            int64_t stride, int64_t batch, tri_dtype dtype, void *stream);
@@ -177,8 +181,9 @@ TRI_API tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int6
  * into the `uplo` triangle of dt (the diagonal is set to 0 for TRI_UNIT); the other
  * triangle of dt is not written.  All matrices column-major, device memory; x, g and dt
  * must not overlap.  TRI_F32 / TRI_F64: CUDA-core products; TRI_F32_MIXED: split-BF16
- * tensor-core products (three terms) for n >= 256.  Scratch: n*n elements per matrix
- * (plus BF16 planes for TRI_F32_MIXED), from the stream-ordered allocator or `_ex`.
+ * tensor-core products (three terms) for n >= 256, one launch per product for a chunk of
+ * the batch whose planes fit in 4 GiB.  Scratch: n*n elements per matrix (plus the BF16
+ * planes of one chunk for TRI_F32_MIXED), from the stream-ordered allocator or `_ex`.
  * --------------------------------------------------------------------------------- */
 TRI_API tri_status tri_inv_backward(tri_uplo uplo, tri_diag diag, int64_t n, const void *x, int64_t ldx,
                                     const void *g, int64_t ldg, void *dt, int64_t lddt, tri_dtype dtype,

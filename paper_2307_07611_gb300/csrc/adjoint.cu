@@ -18,8 +18,9 @@ namespace triinv {
 
 tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
                             int64_t lda, void *ws, int64_t hmax);
-tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws);
-size_t mixed_ws_bytes(int64_t n);
+tri_status run_mixed_batched(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, int64_t stride,
+                             int64_t batch, void *ws);
+size_t mixed_batched_ws_bytes(int64_t n, int64_t batch);
 
 namespace {
 
@@ -52,7 +53,7 @@ tri_status run_plain_batched(const Ctx &c, tri_dtype dt, bool trans, bool unit, 
 
 size_t backward_ws(int64_t n, int64_t batch, tri_dtype dt) {
     size_t m = al((size_t)n * n * esz(dt) * (size_t)batch);
-    if (dt == TRI_F32_MIXED) m += al(gemm_tc_ws_bytes(n, n, n));
+    if (dt == TRI_F32_MIXED) m += al(gemm_tc_ws_bytes(n, n, n, batch));
     return m;
 }
 
@@ -99,8 +100,8 @@ extern "C" {
 
 size_t tri_inv_strided_batched_workspace_size(int64_t n, int64_t batch, tri_dtype dtype) {
     if (n <= 0 || batch <= 0 || bad_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
-    if (dtype == TRI_F32_MIXED) return mixed_ws_bytes(n);
-    return plain_level_ws(n, dtype) * (size_t)batch;
+    if (dtype == TRI_F32_MIXED && n > 256) return mixed_batched_ws_bytes(n, batch);
+    return plain_level_ws(n, dtype == TRI_F64 ? TRI_F64 : TRI_F32) * (size_t)batch;
 }
 
 tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
@@ -116,12 +117,10 @@ tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, v
     tri_status st = device_ctx_public((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
     const bool trans = uplo == TRI_UPPER, unit = diag == TRI_UNIT;
-    if (dtype == TRI_F32_MIXED) {
-        for (int64_t b = 0; b < batch && st == TRI_OK; ++b)
-            st = run_mixed(c, trans, unit, n, (float *)a + b * stride, lda, workspace);
-        return st;
-    }
-    return run_plain_batched(c, dtype, trans, unit, n, a, lda, stride, batch, workspace);
+    // Mixed: one launch per product for a whole chunk of matrices (the FP32 levels below
+    // the tensor-core size).
+    if (dtype == TRI_F32_MIXED && n > 256) return run_mixed_batched(c, trans, unit, n, (float *)a, lda, stride, batch, workspace);
+    return run_plain_batched(c, dtype == TRI_F64 ? TRI_F64 : TRI_F32, trans, unit, n, a, lda, stride, batch, workspace);
 }
 
 tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, int64_t stride,

@@ -75,11 +75,13 @@ __device__ __forceinline__ void write_planes(const T *tiles, int nt, int n, long
     }
 }
 
+// info_as >= 0: a zero pivot records info_as (the matrix of a batch) instead of the row.
 template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
 __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
                                              long long ldp, long long ntot, __nv_bfloat16 *q0 = nullptr,
-                                             __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr) {
+                                             __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr,
+                                             long long info_as = -1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = NT / 32;
     const int n = d.n, nt = (n + 31) / 32;
@@ -126,7 +128,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     {
         const int bad = invert_tiles<T, NT>(tiles, wt, nt, n);
         if (bad >= 0 && !UNIT && threadIdx.x == 0)
-            atomicMin(info, row0 >= 0 ? (long long)(row0 + bad) : (long long)d.index);
+            atomicMin(info, info_as >= 0 ? info_as : (row0 >= 0 ? (long long)(row0 + bad) : (long long)d.index));
     }
 
     // Store the lower triangle back (unit diagonal not written), one warp per tile.
@@ -166,18 +168,28 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict_
 
 // The diagonal blocks of one n x n matrix (lower view through TRANS): CTA b inverts rows
 // and columns [256 b, 256 b + 256) in shared memory and, when p0 != nullptr, writes the
-// BF16 planes of that diagonal block.
+// BF16 planes of that diagonal block.  blockIdx.y: matrix of a batch (matrices as_, planes
+// ps elements apart); index0 >= 0: a zero pivot records the matrix index index0 + blockIdx.y
+// instead of the row.
 template <bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long lda, long long n, long long *info,
                                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1,
                                                              __nv_bfloat16 *p2, long long ldp, __nv_bfloat16 *q0,
-                                                             __nv_bfloat16 *q1, __nv_bfloat16 *q2) {
+                                                             __nv_bfloat16 *q1, __nv_bfloat16 *q2,
+                                                             long long as_, long long ps, long long index0) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
     float *wt = tiles + (size_t)BLimits<8>::kTiles * TE;
     const long long r0 = (long long)blockIdx.x * 256;
+    const long long mb = blockIdx.y;
+    if (mb) {
+        a += mb * as_;
+        p0 += mb * ps; p1 += mb * ps; p2 += mb * ps;
+        if (q0) { q0 += mb * ps; q1 += mb * ps; q2 += mb * ps; }
+    }
     BDesc d{a + vidx<TRANS>(r0, r0, lda), lda, (int)min(256ll, n - r0), (int)blockIdx.x};
-    invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n, q0, q1, q2);
+    invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n, q0, q1, q2,
+                                             index0 >= 0 ? index0 + mb : -1);
 }
 
 template <typename T, int MAXT>
@@ -210,9 +222,11 @@ KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *sme
 // original blocks (q*) (used by the mixed path).
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
                                __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
-                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2) {
+                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2, int64_t batch,
+                               int64_t as_, int64_t ps, int64_t index0) {
     const int64_t blocks = (n + 255) / 256;
-    if (blocks <= 0) return cudaSuccess;
+    if (blocks <= 0 || batch <= 0) return cudaSuccess;
+    if (batch > 65535) return cudaErrorInvalidValue;
     const size_t smem = smem_bytes<float, 8>();
     auto k = trans ? (unit ? diag_blocks_kernel<true, true> : diag_blocks_kernel<true, false>)
                    : (unit ? diag_blocks_kernel<false, true> : diag_blocks_kernel<false, false>);
@@ -223,8 +237,9 @@ cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, f
         const double nb = (double)std::min<int64_t>(256, n - 256 * b);
         fl += nb * nb * nb / 3.0;
     }
-    TraceScope ts(c.stream, "diag_blocks", fl, (double)n * 256.0 * (4.0 + 4.0 + 6.0));
-    k<<<(unsigned)blocks, 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp, q0, q1, q2);
+    TraceScope ts(c.stream, "diag_blocks", fl * (double)batch, (double)batch * n * 256.0 * (4.0 + 4.0 + 6.0));
+    k<<<dim3((unsigned)blocks, (unsigned)batch), 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp, q0, q1,
+                                                                       q2, as_, ps, index0);
     return cudaGetLastError();
 }
 

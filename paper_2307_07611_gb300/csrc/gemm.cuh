@@ -42,8 +42,9 @@ cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char 
 
 // Split-BF16 tensor-core product (FP32 data): both operands are split into BF16
 // hi/mid planes inside `ws` and `terms` (1, 3 or 6) pieces are accumulated in FP32.
-// ws must hold gemm_tc_ws_bytes(m, n, k) bytes.
-size_t gemm_tc_ws_bytes(int64_t m, int64_t n, int64_t k);
+// ws must hold gemm_tc_ws_bytes(m, n, k, g.batch) bytes: the operand planes of one chunk
+// of the batch (all matrices of a chunk in one launch).
+size_t gemm_tc_ws_bytes(int64_t m, int64_t n, int64_t k, int64_t batch = 1);
 cudaError_t gemm_tc(const Ctx &c, const GemmArgs &g, int terms, void *ws, const char *trace_name);
 
 }  // namespace triinv

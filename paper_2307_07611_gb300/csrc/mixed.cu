@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <vector>
 
@@ -33,10 +34,12 @@ namespace triinv {
 
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
-                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag);
+                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag, int64_t batch, int64_t as_,
+                                int64_t ps);
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
                                __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
-                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2);
+                               __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2, int64_t batch,
+                               int64_t as_, int64_t ps, int64_t index0);
 
 // Per-device side stream and events used to run two independent kernels concurrently
 // (fork / join through events, so the pair also works inside stream capture).
@@ -68,25 +71,39 @@ constexpr int64_t kLeaf = 64;
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int64_t cdiv(int64_t x, int64_t m) { return (x + m - 1) / m; }
 
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Matrices per workspace chunk of a batch: the planes of at most kChunkBytes at a time.
+constexpr size_t kChunkBytes = size_t(8) << 30;
+
 struct Layout {
     int64_t ldp;
+    size_t plane;                 // bytes of one plane of one matrix (256-aligned)
+    int64_t batch;                // matrices whose planes the workspace holds
     size_t off_t, off_x, off_r, off_w, off_f, total;
 };
 
-// Workspace: T planes (3), X planes (3), R plane, W planes (2, at the positions of the
-// B blocks of T), then the ready counters of the tensor-core launch.
-Layout layout(int64_t n) {
+// Workspace: T planes (3), X planes (3), R plane, W planes (2; single matrix: at the
+// positions of the B blocks of T; batch: the compact h x P*h level layout), each a group of
+// `batch` planes, then the ready counters of the single-launch schedule.
+Layout layout(int64_t n, int64_t batch = 1) {
     Layout L{};
     L.ldp = round_up(std::max<int64_t>(n, 1), 64);
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t plane = al((size_t)L.ldp * (size_t)n * 2);
+    L.plane = al256((size_t)L.ldp * (size_t)n * 2);
+    L.batch = batch;
+    const size_t g = L.plane * (size_t)batch;
     L.off_t = 0;
-    L.off_x = L.off_t + 3 * plane;
-    L.off_r = L.off_x + 3 * plane;
-    L.off_w = L.off_r + plane;
-    L.off_f = L.off_w + 2 * plane;
-    L.total = L.off_f + al(tc::graph_flag_bytes(n));
+    L.off_x = L.off_t + 3 * g;
+    L.off_r = L.off_x + 3 * g;
+    L.off_w = L.off_r + g;
+    L.off_f = L.off_w + 2 * g;
+    L.total = L.off_f + al256(tc::graph_flag_bytes(n));
     return L;
+}
+
+int64_t chunk_matrices(int64_t n, int64_t batch) {
+    const size_t per = 9 * layout(n).plane;
+    return std::max<int64_t>(1, std::min<int64_t>(batch, (int64_t)(kChunkBytes / per)));
 }
 
 struct Launch {
@@ -104,7 +121,7 @@ struct Plan {
 // Schedule of the tensor-core products: "levels" (default) launches one persistent kernel
 // per product (W and X21 per level, R, the update); "graph" runs them all in one launch
 // that follows the tile dependencies (tc_graph.cu).  Chosen once per process from the
-// environment variable TRI_MIXED_SCHEDULE.
+// environment variable TRI_MIXED_SCHEDULE; batches always use "levels".
 bool use_graph_schedule() {
     static const bool g = [] {
         const char *e = std::getenv("TRI_MIXED_SCHEDULE");
@@ -114,11 +131,13 @@ bool use_graph_schedule() {
 }
 
 std::mutex g_plan_mu;
-std::map<std::pair<int, int64_t>, Plan> g_plans;
+std::map<std::tuple<int, int64_t, int64_t>, Plan> g_plans;
 
-tri_status build_plan(int dev, int sm_count, int64_t n, Plan **out) {
+// Tile lists of every product for `batch` matrices of order n (each product's tiles of
+// all matrices in one longest-first schedule).
+tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto key = std::make_pair(dev, n);
+    auto key = std::make_tuple(dev, n, batch);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {
         *out = &it->second;
@@ -128,11 +147,19 @@ tri_status build_plan(int dev, int sm_count, int64_t n, Plan **out) {
     std::vector<tc::Tile> v;
     std::vector<int> offs;
     auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms) {
+        // replicate the single-matrix tiles over the batch
+        const size_t one_count = v.size() - from;
+        for (int64_t b = 1; b < batch; ++b)
+            for (size_t i = 0; i < one_count; ++i) {
+                tc::Tile t = v[from + i];
+                t.b = (int)b;
+                v.push_back(t);
+            }
         std::vector<tc::Tile> part(v.begin() + from, v.end());
         std::vector<int> o;
         const int ctas = part.empty() ? 0 : tc::schedule_lpt(part, terms, sm_count, o);
         std::copy(part.begin(), part.end(), v.begin() + from);
-        Launch l{(int)from, ctas, (int)offs.size(), flops};
+        Launch l{(int)from, ctas, (int)offs.size(), flops * (double)batch};
         for (int x : o) offs.push_back(x);
         if (vec) vec->push_back(l);
         else *one = l;
@@ -210,27 +237,40 @@ size_t mixed_ws_bytes(int64_t n) {
     return layout(n).total;
 }
 
+// Workspace of the strided-batched mixed path: the planes of one chunk of matrices.
+size_t mixed_batched_ws_bytes(int64_t n, int64_t batch) {
+    if (n <= kDiag) return 0;
+    return layout(n, chunk_matrices(n, batch)).total;
+}
+
 tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
                             int64_t lda, void *ws, int64_t hmax);
 
-tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws) {
-    if (n <= kDiag) return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
-    const Layout L = layout(n);
+namespace {
+
+// One chunk of `batch` matrices (stride elements apart) whose planes fit the workspace.
+// index0 >= 0: matrices of a batch starting at index index0 (zero pivots report the
+// matrix index); -1: a single matrix (zero pivots report the row).
+tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, int64_t stride,
+                           int64_t batch, int64_t index0, void *ws) {
+    const Layout L = layout(n, batch);
     uint8_t *base = (uint8_t *)ws;
-    const size_t plane = ((size_t)L.ldp * (size_t)n * 2 + 255) / 256 * 256;
+    const size_t g = L.plane * (size_t)batch;   // bytes of one plane group
+    const int64_t ps = (int64_t)(L.plane / 2);  // elements between the planes of consecutive matrices
     __nv_bfloat16 *T[3], *X[3], *R[1], *W[2];
     for (int i = 0; i < 3; ++i) {
-        T[i] = (__nv_bfloat16 *)(base + L.off_t + i * plane);
-        X[i] = (__nv_bfloat16 *)(base + L.off_x + i * plane);
+        T[i] = (__nv_bfloat16 *)(base + L.off_t + i * g);
+        X[i] = (__nv_bfloat16 *)(base + L.off_x + i * g);
     }
     R[0] = (__nv_bfloat16 *)(base + L.off_r);
     W[0] = (__nv_bfloat16 *)(base + L.off_w);
-    W[1] = (__nv_bfloat16 *)(base + L.off_w + plane);
+    W[1] = (__nv_bfloat16 *)(base + L.off_w + g);
 
-    const bool graph = use_graph_schedule();
+    const bool graph = batch == 1 && use_graph_schedule();
     const tc::GraphPlan *gplan = nullptr;
     Plan *plan = nullptr;
-    tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan) : build_plan(c.device, c.sm_count, n, &plan);
+    tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan)
+                          : build_plan(c.device, c.sm_count, n, batch, &plan);
     if (st != TRI_OK) return st;
 
     // 1. T planes of the off-diagonal part (side stream), concurrently with
@@ -244,9 +284,11 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         return TRI_ERR_CUDA;
     Ctx cs = c;
     cs.stream = ss->s;
-    if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true) != cudaSuccess)
+    if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps) !=
+        cudaSuccess)
         return TRI_ERR_CUDA;
-    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2]) != cudaSuccess)
+    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2], batch, stride, ps,
+                           index0) != cudaSuccess)
         return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
@@ -260,7 +302,10 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         return tc::launch_graph(c, trans, unit, n, *gplan, T, ep) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
     }
     auto pl = [&](const __nv_bfloat16 *p, int64_t rows, int64_t cols, int64_t ld) {
-        return tc::Plane{p, rows, cols, ld};
+        tc::Plane q{p, rows, cols, ld};
+        q.batch = batch;
+        q.bstride = ps;
+        return q;
     };
     const tc::Plane tp[3] = {pl(T[0], n, n, L.ldp), pl(T[1], n, n, L.ldp), pl(T[2], n, n, L.ldp)};
     const tc::Plane xp[3] = {pl(X[0], n, n, L.ldp), pl(X[1], n, n, L.ldp), pl(X[2], n, n, L.ldp)};
@@ -271,11 +316,14 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
         const int64_t P = level_pairs(n, h);
         const tc::Plane wp[2] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h)};
         tc::Epi ew{nullptr, 0, W[0], W[1], nullptr, h, h, P * h};
+        ew.os = ps;
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, tc::MODE_W, trans, unit, tp, 3, xp, 3, three, plan->d_tiles + lw.first,
                           plan->d_off + lw.off_first, lw.ctas, ew, lw.flops, "tc_gemm:w") != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
+        ex.xs = stride;
+        ex.os = ps;
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, tc::MODE_X21, trans, unit, xp, 3, wp, 2, three, plan->d_tiles + lx.first,
                           plan->d_off + lx.off_first, lx.ctas, ex, lx.flops, "tc_gemm:x21") != cudaSuccess)
@@ -284,15 +332,37 @@ tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, i
     // 5. Newton-Schulz: R = I - T X, then X += X R
     const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
     tc::Epi er{nullptr, 0, R[0], nullptr, nullptr, L.ldp, n, n};
+    er.os = ps;
     if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
                       plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
         return TRI_ERR_CUDA;
     const tc::Plane rp[1] = {pl(R[0], n, n, L.ldp)};
     const tc::Terms one{1, {0}, {0}};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
+    eu.xs = stride;
     if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + plan->upd.first,
                       plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
         return TRI_ERR_CUDA;
+    return TRI_OK;
+}
+
+}  // namespace
+
+tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws) {
+    if (n <= kDiag) return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
+    return run_mixed_chunk(c, trans, unit, n, a, lda, 0, 1, -1, ws);
+}
+
+// `batch` matrices `stride` elements apart (n > 256), in chunks whose planes fit the
+// workspace of mixed_batched_ws_bytes(n, batch).
+tri_status run_mixed_batched(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, int64_t stride,
+                             int64_t batch, void *ws) {
+    const int64_t cb = chunk_matrices(n, batch);
+    for (int64_t b0 = 0; b0 < batch; b0 += cb) {
+        const tri_status st =
+            run_mixed_chunk(c, trans, unit, n, a + b0 * stride, lda, stride, std::min(cb, batch - b0), b0, ws);
+        if (st != TRI_OK) return st;
+    }
     return TRI_OK;
 }
 

@@ -27,7 +27,8 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
 
 // One 64 x 64 tile per CTA.  DIAG_ONLY: blockIdx.z is the diagonal 256-block and
 // (blockIdx.x, blockIdx.y) the tile inside it; otherwise (blockIdx.x, blockIdx.y) is the
-// tile of the whole matrix and tiles that no product reads return at once.
+// tile of the whole matrix, blockIdx.z the matrix of a batch (source as_ and planes ps
+// elements apart), and tiles that no product reads return at once.
 // Thread t owns rows (2*(t%32), 2*(t%32)+1) of the tile and columns t/32 + 8*c, so a warp
 // stores 64 consecutive rows (128 bytes per plane) per column.
 template <bool TRANS, bool UNIT, bool DIAG_ONLY>
@@ -35,8 +36,14 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
                                                     __nv_bfloat16 *__restrict__ p0,
                                                     __nv_bfloat16 *__restrict__ p1,
                                                     __nv_bfloat16 *__restrict__ p2, int64_t ldp,
-                                                    bool skip_diag) {
+                                                    bool skip_diag, int64_t as_, int64_t ps) {
     int64_t i0, j0;
+    if (!DIAG_ONLY && blockIdx.z) {
+        a += (int64_t)blockIdx.z * as_;
+        p0 += (int64_t)blockIdx.z * ps;
+        p1 += (int64_t)blockIdx.z * ps;
+        p2 += (int64_t)blockIdx.z * ps;
+    }
     if (DIAG_ONLY) {
         i0 = (int64_t)blockIdx.z * 256 + blockIdx.x * TS;
         j0 = (int64_t)blockIdx.z * 256 + blockIdx.y * TS;
@@ -103,14 +110,22 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
 
 // Rectangle rows x cols (column-major, lds) -> planes, with the triangle kind of the
 // operand applied (0 outside the stored triangle, 1 on an implicit unit diagonal).
-// Thread t owns rows 2*(t%32), 2*(t%32)+1 of a 64-row strip; blockIdx.y = 8-column group.
+// Thread t owns rows 2*(t%32), 2*(t%32)+1 of a 64-row strip; blockIdx.y = 8-column group;
+// blockIdx.z = matrix of a batch (source as_ and planes ps elements apart).
 template <bool TR>
 __global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict__ a, int64_t lds,
                                                          int64_t rows, int64_t cols, int kind,
                                                          __nv_bfloat16 *__restrict__ p0,
                                                          __nv_bfloat16 *__restrict__ p1,
-                                                         __nv_bfloat16 *__restrict__ p2, int64_t ldp) {
+                                                         __nv_bfloat16 *__restrict__ p2, int64_t ldp,
+                                                         int64_t as_, int64_t ps) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.z) {
+        a += (int64_t)blockIdx.z * as_;
+        p0 += (int64_t)blockIdx.z * ps;
+        p1 += (int64_t)blockIdx.z * ps;
+        if (p2) p2 += (int64_t)blockIdx.z * ps;
+    }
     const int64_t i = (int64_t)blockIdx.x * 64 + 2 * lane;
     const int64_t j = (int64_t)blockIdx.y * 8 + w;
     if (i >= rows || j >= cols) return;
@@ -148,24 +163,29 @@ __global__ void __launch_bounds__(256) split_rect_kernel(const float *__restrict
 
 cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t rows, int64_t cols,
                               int kind, __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
-                              int64_t ldp, bool trans) {
-    if (rows <= 0 || cols <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((cols + 7) / 8));
-    TraceScope ts(c.stream, "split_rect", 0.0, (double)rows * cols * (4.0 + (p2 ? 6.0 : 4.0)));
-    if (trans) split_rect_kernel<true><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
-    else split_rect_kernel<false><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp);
+                              int64_t ldp, bool trans, int64_t batch, int64_t as_, int64_t ps) {
+    if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
+    if (batch > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((cols + 7) / 8), (unsigned)batch);
+    TraceScope ts(c.stream, "split_rect", 0.0, (double)batch * rows * cols * (4.0 + (p2 ? 6.0 : 4.0)));
+    if (trans) split_rect_kernel<true><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp, as_, ps);
+    else split_rect_kernel<false><<<grid, 256, 0, c.stream>>>(a, lds, rows, cols, kind, p0, p1, p2, ldp, as_, ps);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
-                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag) {
+                                __nv_bfloat16 *p2, int64_t ldp, bool skip_diag, int64_t batch,
+                                int64_t as_, int64_t ps) {
     const int64_t t = (n + TS - 1) / TS;
-    if (t <= 0) return cudaSuccess;
-    dim3 grid = diag_only ? dim3(256 / TS, 256 / TS, (unsigned)((n + 255) / 256)) : dim3((unsigned)t, (unsigned)t);
-    const double elems = diag_only ? (double)n * 256.0 : (double)n * n / 2.0;
+    if (t <= 0 || batch <= 0) return cudaSuccess;
+    if (batch > 65535 || (diag_only && batch > 1)) return cudaErrorInvalidValue;
+    dim3 grid = diag_only ? dim3(256 / TS, 256 / TS, (unsigned)((n + 255) / 256))
+                          : dim3((unsigned)t, (unsigned)t, (unsigned)batch);
+    const double elems = (diag_only ? (double)n * 256.0 : (double)n * n / 2.0) * (double)batch;
     TraceScope ts(c.stream, diag_only ? "split_diag" : "split_t", 0.0, elems * (4.0 + 6.0));
-#define TRI_SPLIT(TR, UN, DO) split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp, skip_diag)
+#define TRI_SPLIT(TR, UN, DO) \
+    split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp, skip_diag, as_, ps)
     if (diag_only) {
         if (trans) { if (unit) TRI_SPLIT(true, true, true); else TRI_SPLIT(true, false, true); }
         else { if (unit) TRI_SPLIT(false, true, true); else TRI_SPLIT(false, false, true); }

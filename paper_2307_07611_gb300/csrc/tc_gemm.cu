@@ -52,13 +52,13 @@ struct Maps {
 // Column-major targets advance by one leading dimension per column, so the 32 threads of
 // a warp (32 consecutive rows) write contiguous bytes for every column.
 template <int MODE, bool TRANS, bool UNIT, int NC>
-__device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t gn0,
+__device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t ob, int64_t gm, int64_t gn0,
                                               const uint32_t (&r)[NC]) {
     if (gm >= ep.mlim) return;
     const int64_t left = ep.nlim - gn0;
     if (MODE == MODE_W || MODE == MODE_X21 || MODE == MODE_RES) {
-        int64_t off = gm + gn0 * ep.ldo;
-        int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+        int64_t off = ob + gm + gn0 * ep.ldo;
+        int64_t xo = xb + vidx<TRANS>(gm, gn0, ep.ldx);
         const int64_t xstep = TRANS ? 1 : ep.ldx;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -83,7 +83,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
             xo += xstep;
         }
     } else if (MODE == MODE_UPD) {
-        int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+        int64_t xo = xb + vidx<TRANS>(gm, gn0, ep.ldx);
         const int64_t xstep = TRANS ? 1 : ep.ldx;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -92,7 +92,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
             xo += xstep;
         }
     } else if (MODE == MODE_GEN) {
-        int64_t xo = gm + gn0 * ep.ldx;
+        int64_t xo = xb + gm + gn0 * ep.ldx;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             const int64_t gn = gn0 + j;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
             xo += ep.ldx;
         }
     } else {
-        int64_t xo = gm + gn0 * ep.ldx;
+        int64_t xo = xb + gm + gn0 * ep.ldx;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
             if (j < left) ep.x[xo] = __uint_as_float(r[j]);
@@ -118,8 +118,8 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t gm, int64_t
 // X values of row gm, columns gn0..gn0+15, that the update touches (lower triangle,
 // and the diagonal unless unit); others read as 0 and are not stored.
 template <bool TRANS, bool UNIT>
-__device__ __forceinline__ void load_x16(const Epi &ep, int64_t gm, int64_t gn0, float (&xv)[16]) {
-    int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+__device__ __forceinline__ void load_x16(const Epi &ep, int64_t xb, int64_t gm, int64_t gn0, float (&xv)[16]) {
+    int64_t xo = xb + vidx<TRANS>(gm, gn0, ep.ldx);
     const int64_t xstep = TRANS ? 1 : ep.ldx;
     const bool row_ok = gm < ep.mlim;
 #pragma unroll
@@ -131,10 +131,10 @@ __device__ __forceinline__ void load_x16(const Epi &ep, int64_t gm, int64_t gn0,
 }
 
 template <bool TRANS, bool UNIT>
-__device__ __forceinline__ void store_upd16(const Epi &ep, int64_t gm, int64_t gn0, const float (&xv)[16],
-                                            const uint32_t (&r)[16]) {
+__device__ __forceinline__ void store_upd16(const Epi &ep, int64_t xb, int64_t gm, int64_t gn0,
+                                            const float (&xv)[16], const uint32_t (&r)[16]) {
     if (gm >= ep.mlim) return;
-    int64_t xo = vidx<TRANS>(gm, gn0, ep.ldx);
+    int64_t xo = xb + vidx<TRANS>(gm, gn0, ep.ldx);
     const int64_t xstep = TRANS ? 1 : ep.ldx;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -175,6 +175,7 @@ struct Pipe {
     int na, nb;          // A / B tiles per stage
     int stages;          // ring depth
     int stage_bytes;     // na * BM * ks * 2 + nb * BN * ks * 2
+    int batched;         // maps are 3-D (batch outermost): loads take the tile's matrix
 };
 
 template <int MODE, bool TRANS, bool UNIT>
@@ -211,11 +212,18 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
         for (int i = 0; i < na; ++i) {
             const uint32_t dst = st + (uint32_t)(i * A_TILE);
 #pragma unroll
-            for (int c = 0; c < BM / 64; ++c)
-                tma_load_2d(dst + (uint32_t)(c * KS * 128), &maps.a[ia0 + i], tl.am + 64 * c, tl.ak + k, bar);
+            for (int c = 0; c < BM / 64; ++c) {
+                if (pipe.batched)
+                    tma_load_3d(dst + (uint32_t)(c * KS * 128), &maps.a[ia0 + i], tl.am + 64 * c, tl.ak + k, tl.b, bar);
+                else
+                    tma_load_2d(dst + (uint32_t)(c * KS * 128), &maps.a[ia0 + i], tl.am + 64 * c, tl.ak + k, bar);
+            }
         }
-        for (int i = 0; i < nb; ++i)
-            tma_load_2d(st + (uint32_t)(na * A_TILE + i * B_TILE), &maps.b[ib0 + i], tl.bk + k, tl.bn, bar);
+        for (int i = 0; i < nb; ++i) {
+            const uint32_t dst = st + (uint32_t)(na * A_TILE + i * B_TILE);
+            if (pipe.batched) tma_load_3d(dst, &maps.b[ib0 + i], tl.bk + k, tl.bn, tl.b, bar);
+            else tma_load_2d(dst, &maps.b[ib0 + i], tl.bk + k, tl.bn, bar);
+        }
     };
     // MMAs of one term on stage tiles sa / sb (KS / 16 steps of K = 16).
     auto mma_term = [&](uint32_t d, uint32_t sa, uint32_t sb, uint32_t &accumulate) {
@@ -382,6 +390,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             const Tile tl = tiles[t];
             const int cb = chunk_blocks(tl);
             const int64_t gm = (int64_t)tl.om + row;
+            const int64_t xb = (int64_t)tl.b * ep.xs, ob = (int64_t)tl.b * ep.os;
             float sum[PROMOTE ? BN / 2 : 1];
             if (PROMOTE) {
 #pragma unroll
@@ -390,7 +399,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             // The update reads X: fetch the first 16 columns before the accumulator is ready.
             const int64_t gcol0 = (int64_t)tl.on + half * (BN / 2);
             float xv[MODE == MODE_UPD ? 16 : 1];
-            if (MODE == MODE_UPD) load_x16<TRANS, UNIT>(ep, gm, gcol0, *(float(*)[16])xv);
+            if (MODE == MODE_UPD) load_x16<TRANS, UNIT>(ep, xb, gm, gcol0, *(float(*)[16])xv);
             for (int c0 = tl.kb0; c0 < tl.kb1; c0 += cb, ++lc) {
                 const uint32_t a = lc & 1u, use = lc >> 1;
                 if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
@@ -415,10 +424,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     for (int q = 0; q < BN / 32; ++q) {
                         float xn[16];
                         if (q + 1 < BN / 32)
-                            load_x16<TRANS, UNIT>(ep, gm, gcol0 + (q + 1) * 16, xn);
+                            load_x16<TRANS, UNIT>(ep, xb, gm, gcol0 + (q + 1) * 16, xn);
                         uint32_t r[16];
                         tmem_ld16(taddr + q * 16, r);
-                        store_upd16<TRANS, UNIT>(ep, gm, gcol0 + q * 16, *(float(*)[16])xv, r);
+                        store_upd16<TRANS, UNIT>(ep, xb, gm, gcol0 + q * 16, *(float(*)[16])xv, r);
                         if (q + 1 < BN / 32) {
 #pragma unroll
                             for (int i = 0; i < 16; ++i) xv[i] = xn[i];
@@ -429,7 +438,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     for (int q = 0; q < BN / 16; ++q) {
                         uint32_t r[8];
                         tmem_ld8(taddr + q * 8, r);
-                        epilogue_cols<MODE, TRANS, UNIT, 8>(ep, gm, gcol0 + q * 8, r);
+                        epilogue_cols<MODE, TRANS, UNIT, 8>(ep, xb, ob, gm, gcol0 + q * 8, r);
                     }
                 }
                 tc_fence_before();
@@ -442,7 +451,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     uint32_t r[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(sum[q * 16 + i]);
-                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, gm, (int64_t)tl.on + half * (BN / 2) + q * 16, r);
+                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, xb, ob, gm, (int64_t)tl.on + half * (BN / 2) + q * 16, r);
                 }
             }
         }
@@ -504,21 +513,19 @@ bool get_encode() {
 // swizzle, box = box_rows x box_cols, zero fill outside [0, rows) x [0, cols).
 bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols, bool swizzle64) {
     if (!get_encode()) return false;
-    if (((uintptr_t)p.p & 15) || (p.ld * 2) % 16 || p.rows <= 0 || p.cols <= 0) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)p.rows, (cuuint64_t)p.cols};
-    cuuint64_t strides[1] = {(cuuint64_t)(p.ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)p.p, dims, strides, box, estr,
+    if (((uintptr_t)p.p & 15) || (p.ld * 2) % 16 || p.rows <= 0 || p.cols <= 0 || p.batch < 1) return false;
+    if (p.batch > 1 && ((p.bstride * 2) % 16 || p.bstride < p.ld * p.cols)) return false;
+    const cuuint32_t rank = p.batch > 1 ? 3 : 2;
+    cuuint64_t dims[3] = {(cuuint64_t)p.rows, (cuuint64_t)p.cols, (cuuint64_t)p.batch};
+    cuuint64_t strides[2] = {(cuuint64_t)(p.ld * 2), (cuuint64_t)(p.bstride * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, (void *)p.p, dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
                           swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
-
-namespace {
-
-}  // namespace
 
 int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int> &offsets) {
     const int nt = (int)tiles.size();
@@ -573,7 +580,7 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         if (!encode_plane(&maps.b[i], pb, cf.ks, BN, cf.ks == 32)) return cudaErrorInvalidValue;
     }
     // Stage layout: every distinct plane the terms read (fused), or one term's pair.
-    Pipe pipe{1, 1, 0, 0};
+    Pipe pipe{1, 1, 0, 0, 0};
     for (int j = 0; j < terms.n; ++j) {
         if (terms.a[j] < 0 || terms.a[j] >= na || terms.b[j] < 0 || terms.b[j] >= nb) return cudaErrorInvalidValue;
         if (cf.fused) {
@@ -582,6 +589,11 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         }
     }
     pipe.stage_bytes = (pipe.na * BM + pipe.nb * BN) * cf.ks * 2;
+    pipe.batched = aplanes[0].batch > 1 ? 1 : 0;
+    for (int i = 0; i < na; ++i)
+        if ((aplanes[i].batch > 1) != (pipe.batched != 0)) return cudaErrorInvalidValue;
+    for (int i = 0; i < nb; ++i)
+        if ((bplanes[i].batch > 1) != (pipe.batched != 0)) return cudaErrorInvalidValue;
     pipe.stages = std::min(MAX_STAGES, STAGE_BUDGET / pipe.stage_bytes);
     TraceScope ts(c.stream, trace_name, flops, 0.0);
 #define TRI_TC_CASE(M)                                                                   \

@@ -16,9 +16,11 @@ constexpr int BN = 256;   // columns of an output tile (UMMA N)
 constexpr int BK = 64;    // k-block staged per pipeline slot (one 128-byte swizzle row)
 
 // One output tile: operand A rows [am, am+128) and columns ak + [kb0*64, kb1*64);
-// operand B rows bk + [kb0*64, kb1*64) and columns [bn, bn+256); output origin (om, on).
+// operand B rows bk + [kb0*64, kb1*64) and columns [bn, bn+256); output origin (om, on);
+// b: matrix of a batch (planes and outputs offset by b times their batch strides).
 struct Tile {
     int am, ak, bk, bn, kb0, kb1, om, on;
+    int b = 0;
 };
 
 // Products summed into one FP32 accumulator: sum_t A_{a[t]} * B_{b[t]}.
@@ -38,6 +40,7 @@ struct Epi {
     float alpha = 1.f, beta = 0.f; // MODE_GEN: x <- alpha * acc + beta * x
     int cmask = 0;                 // MODE_GEN: part of x written: 0 full, 1 lower, 2 upper,
                                    // 3 / 4 strict lower / upper with a zero diagonal
+    int64_t xs = 0, os = 0;        // batch strides (elements) of x and of the output planes
 };
 
 enum Mode {
@@ -51,13 +54,16 @@ enum Mode {
 
 // A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld
 // (elements, multiple of 8), device pointer 16-byte aligned.
+// batch > 1: `batch` such planes, bstride elements apart (multiple of 8).
 struct Plane {
     const __nv_bfloat16 *p;
     int64_t rows, cols, ld;
+    int64_t batch = 1, bstride = 0;
 };
 
-// Encodes a 2-D TMA map over a column-major BF16 plane (inner dimension = rows, 128-byte
-// or 64-byte swizzle, zero fill outside the plane) with box box_rows x box_cols.  False if the
+// Encodes a TMA map over a column-major BF16 plane (inner dimension = rows, 128-byte or
+// 64-byte swizzle, zero fill outside the plane) with box box_rows x box_cols: 2-D, or
+// 3-D with the batch as the outer dimension (box depth 1) when p.batch > 1.  False if the
 // driver entry point is missing or the plane violates the TMA alignment rules.
 bool encode_plane(CUtensorMap *m, const Plane &p, int box_rows, int box_cols, bool swizzle64 = false);
 
