@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(GCfg<T, BM, BN, BK, TM, TN>::NT)
 gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__ A, int64_t lda,
                  int akind, const T *__restrict__ B, int64_t ldb, int bkind, T beta, T *C,
                  int64_t ldc, int cmask, int64_t sa, int64_t sb, int64_t sc, int64_t nb1,
-                 int64_t sa2, int64_t sb2, int64_t sc2) {
+                 int64_t sa2, int64_t sb2, int64_t sc2, int ksplit) {
     using Cf = GCfg<T, BM, BN, BK, TM, TN>;
     constexpr int NT = Cf::NT;
     __shared__ __align__(16) T As[2][BK][BM + Cf::PAD];
@@ -54,8 +54,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     const int m0 = blockIdx.y * BM;
     const int n0 = blockIdx.x * BN;
     if (m0 >= M || n0 >= N) return;
+    // blockIdx.z = matrix * ksplit + k slice
+    const int ks = (int)(blockIdx.z % ksplit);
     {
-        const int64_t inner = blockIdx.z % nb1, outer = blockIdx.z / nb1;
+        const int64_t z = blockIdx.z / ksplit;
+        const int64_t inner = z % nb1, outer = z / nb1;
         A += inner * sa + outer * sa2;
         B += inner * sb + outer * sb2;
         C += inner * sc + outer * sc2;
@@ -77,6 +80,15 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     if (a_up) kbeg = max(kbeg, (m0 / BK) * BK);    // op(A)(m,k) = 0 for k < m
     if (b_low) kbeg = max(kbeg, (n0 / BK) * BK);   // op(B)(k,n) = 0 for k < n
     if (b_up) kend = min(kend, n0 + BN);           // op(B)(k,n) = 0 for k > n
+    if (ksplit > 1) {
+        // this CTA's slice of the k range (whole BK steps); the slices add into a C that
+        // was zeroed before the launch
+        const int len = ((kend - kbeg + ksplit - 1) / ksplit + BK - 1) / BK * BK;
+        const int kb = kbeg + ks * len;
+        kend = min(kend, kb + len);
+        kbeg = kb;
+        if (kbeg >= kend) return;
+    }
 
     // Thread -> element maps follow the contiguous index of each operand in memory.
     // Each thread keeps a pointer per loaded element and advances it by one k-slice per
@@ -181,30 +193,70 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
             if (c_up && gm > gn) continue;
             T *c = C + gm + (int64_t)gn * ldc;
             if ((cmask == OP_LOWER_UNIT || cmask == OP_UPPER_UNIT) && gm == gn) {
-                *c = T(0);
+                if (ksplit == 1) *c = T(0);
                 continue;
             }
-            *c = beta == T(0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+            if (ksplit > 1) atomicAdd(c, alpha * acc[i][j]);
+            else *c = beta == T(0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
         }
     }
 }
 
+// Zeroes the part of C (M x N per matrix) that a product with output mask cmask writes.
+template <typename T>
+__global__ void zero_masked_kernel(T *C, int64_t M, int64_t N, int64_t ldc, int cmask, int64_t sc, int64_t nb1,
+                                   int64_t sc2) {
+    const int64_t gm = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gn = blockIdx.y;
+    if (gm >= M) return;
+    const bool c_low = cmask == OP_LOWER || cmask == OP_LOWER_UNIT;
+    const bool c_up = cmask == OP_UPPER || cmask == OP_UPPER_UNIT;
+    if ((c_low && gn > gm) || (c_up && gm > gn)) return;
+    const int64_t z = blockIdx.z, inner = z % nb1, outer = z / nb1;
+    C[inner * sc + outer * sc2 + gm + gn * ldc] = T(0);
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, bool TB>
-cudaError_t launch_g2(const Ctx &c, const GemmArgs &g) {
+cudaError_t launch_g2(const Ctx &c, const GemmArgs &g, int ksplit) {
     using Cf = GCfg<T, BM, BN, BK, TM, TN>;
-    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM), (unsigned)(g.batch * g.batch2));
+    const int64_t mats = g.batch * g.batch2;
+    if (ksplit > 1) {
+        if (g.n > 65535) return cudaErrorInvalidValue;
+        dim3 zg((unsigned)((g.m + 255) / 256), (unsigned)g.n, (unsigned)mats);
+        zero_masked_kernel<T><<<zg, 256, 0, c.stream>>>((T *)g.c, g.m, g.n, g.ldc, g.cmask, g.sc, g.batch, g.sc2);
+    }
+    dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM), (unsigned)(mats * ksplit));
     gemm_simt_kernel<T, BM, BN, BK, TM, TN, TA, TB><<<grid, Cf::NT, 0, c.stream>>>(
         g.m, g.n, g.k, (T)g.alpha, (const T *)g.a, g.lda, g.akind, (const T *)g.b, g.ldb, g.bkind,
-        (T)g.beta, (T *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc, g.batch, g.sa2, g.sb2, g.sc2);
+        (T)g.beta, (T *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc, g.batch, g.sa2, g.sb2, g.sc2, ksplit);
     return cudaGetLastError();
 }
 
 template <typename T, int BM, int BN, int BK, int TM, int TN>
-cudaError_t launch_g(const Ctx &c, const GemmArgs &g) {
-    if (g.ta) return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, true, true>(c, g)
-                          : launch_g2<T, BM, BN, BK, TM, TN, true, false>(c, g);
-    return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, false, true>(c, g)
-                : launch_g2<T, BM, BN, BK, TM, TN, false, false>(c, g);
+cudaError_t launch_g(const Ctx &c, const GemmArgs &g, int ksplit = 1) {
+    if (g.ta) return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, true, true>(c, g, ksplit)
+                          : launch_g2<T, BM, BN, BK, TM, TN, true, false>(c, g, ksplit);
+    return g.tb ? launch_g2<T, BM, BN, BK, TM, TN, false, true>(c, g, ksplit)
+                : launch_g2<T, BM, BN, BK, TM, TN, false, false>(c, g, ksplit);
+}
+
+// FP64 products run on a part with little FP64 throughput per SM: small tiles, and the k
+// range split over several CTAs (atomic adds into a zeroed C) until the grid covers about
+// two waves of the SMs.  Split only when beta == 0; C never overlaps A or B in the callers
+// (level products write the workspace or the B block they no longer read).
+cudaError_t launch_f64(const Ctx &c, const GemmArgs &g) {
+    const bool small = g.m <= 128 || g.n <= 128;
+    const int64_t bm = small ? 32 : 64;
+    const int64_t tiles = ((g.m + bm - 1) / bm) * ((g.n + bm - 1) / bm) * g.batch * g.batch2;
+    int ksplit = 1;
+    if (g.beta == 0.0 && tiles < 2 * (int64_t)c.sm_count) {
+        const int64_t want = (2 * (int64_t)c.sm_count + tiles - 1) / tiles;
+        const int64_t most = std::max<int64_t>(1, g.k / 64);   // at least 64 k per slice
+        ksplit = (int)std::min<int64_t>({want, most, 16, 65535 / (g.batch * g.batch2)});
+        ksplit = std::max(ksplit, 1);
+    }
+    if (small) return launch_g<double, 32, 32, 16, 2, 2>(c, g, ksplit);
+    return launch_g<double, 64, 64, 16, 4, 4>(c, g, ksplit);
 }
 
 }  // namespace
@@ -227,7 +279,7 @@ cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char 
     if (g.batch * g.batch2 > 65535 || g.m >= (1ll << 31) || g.n >= (1ll << 31) || g.k >= (1ll << 31))
         return cudaErrorInvalidValue;
     TraceScope ts(c.stream, trace_name, gemm_flops(g) * (double)(g.batch * g.batch2), 0.0);
-    if (dt == TRI_F64) return launch_g<double, 64, 64, 16, 4, 4>(c, g);
+    if (dt == TRI_F64) return launch_f64(c, g);
     if (g.m >= 128 && g.n >= 128) return launch_g<float, 128, 128, 8, 8, 8>(c, g);
     return launch_g<float, 64, 64, 16, 4, 4>(c, g);
 }
