@@ -133,14 +133,17 @@ TraceScope::~TraceScope() {
 // ---- plans ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kLeafPlain = 64;
+// Leaf order of the plain path.  FP64 leaves are 16: GB300 has little FP64 throughput per
+// SM, so the serial leaf recurrence is kept short and the work moves into the level
+// products, which spread over every SM.
+int leaf_plain(tri_dtype dt) { return dt == TRI_F64 ? 16 : 64; }
 
 size_t elem_size(tri_dtype dt) { return dt == TRI_F64 ? 8 : 4; }
 
 // Largest per-level scratch of the plain path: one h x h W block per active pair.
 size_t plain_ws_bytes(int64_t n, tri_dtype dt) {
     size_t best = 0;
-    for (int64_t h = kLeafPlain; h < n; h *= 2) {
+    for (int64_t h = leaf_plain(dt); h < n; h *= 2) {
         const int64_t p = level_pairs(n, h);
         best = std::max(best, (size_t)p * (size_t)h * (size_t)h * elem_size(dt));
     }
@@ -160,9 +163,10 @@ tri_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TRI_OK : TRI_ERR
 // recursion; hmax = 256: only the diagonal 256-blocks, as the mixed path needs).
 tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a,
                             int64_t lda, void *ws, int64_t hmax) {
-    cudaError_t e = launch_leaf(c, dt, trans, unit, n, a, lda, kLeafPlain);
+    const int leaf = leaf_plain(dt);
+    cudaError_t e = launch_leaf(c, dt, trans, unit, n, a, lda, leaf);
     if (e != cudaSuccess) return TRI_ERR_CUDA;
-    for (int64_t h = kLeafPlain; h < n && h < hmax; h *= 2) {
+    for (int64_t h = leaf; h < n && h < hmax; h *= 2) {
         e = launch_trmm_level(c, dt, trans, unit, 0, n, a, lda, h, ws);
         if (e != cudaSuccess) return TRI_ERR_CUDA;
         e = launch_trmm_level(c, dt, trans, unit, 1, n, a, lda, h, ws);

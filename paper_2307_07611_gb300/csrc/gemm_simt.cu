@@ -240,23 +240,22 @@ cudaError_t launch_g(const Ctx &c, const GemmArgs &g, int ksplit = 1) {
                 : launch_g2<T, BM, BN, BK, TM, TN, false, false>(c, g, ksplit);
 }
 
-// FP64 products run on a part with little FP64 throughput per SM: small tiles, and the k
-// range split over several CTAs (atomic adds into a zeroed C) until the grid covers about
-// two waves of the SMs.  Split only when beta == 0; C never overlaps A or B in the callers
-// (level products write the workspace or the B block they no longer read).
+// FP64 products run on a part with little FP64 throughput per SM (2 DFMA per clock):
+// 32 x 32 tiles, and the k range split over several CTAs (atomic adds into a zeroed C)
+// until the grid covers about four waves of the SMs.  Split only when beta == 0; C never
+// overlaps A or B in the callers (level products write the workspace or the B block they
+// no longer read).
 cudaError_t launch_f64(const Ctx &c, const GemmArgs &g) {
-    const bool small = g.m <= 128 || g.n <= 128;
-    const int64_t bm = small ? 32 : 64;
-    const int64_t tiles = ((g.m + bm - 1) / bm) * ((g.n + bm - 1) / bm) * g.batch * g.batch2;
+    const int64_t mats = g.batch * g.batch2;
+    const int64_t tiles = ((g.m + 31) / 32) * ((g.n + 31) / 32) * mats;
     int ksplit = 1;
-    if (g.beta == 0.0 && tiles < 2 * (int64_t)c.sm_count) {
-        const int64_t want = (2 * (int64_t)c.sm_count + tiles - 1) / tiles;
-        const int64_t most = std::max<int64_t>(1, g.k / 64);   // at least 64 k per slice
-        ksplit = (int)std::min<int64_t>({want, most, 16, 65535 / (g.batch * g.batch2)});
+    if (g.beta == 0.0 && tiles < 4 * (int64_t)c.sm_count) {
+        const int64_t want = (4 * (int64_t)c.sm_count + tiles - 1) / tiles;
+        const int64_t most = std::max<int64_t>(1, g.k / 16);   // at least one 16-wide k step per slice
+        ksplit = (int)std::min<int64_t>({want, most, 64, 65535 / mats});
         ksplit = std::max(ksplit, 1);
     }
-    if (small) return launch_g<double, 32, 32, 16, 2, 2>(c, g, ksplit);
-    return launch_g<double, 64, 64, 16, 4, 4>(c, g, ksplit);
+    return launch_g<double, 32, 32, 16, 2, 2>(c, g, ksplit);
 }
 
 }  // namespace
