@@ -63,7 +63,10 @@ typedef enum { TRI_LOWER = 0, TRI_UPPER = 1 } tri_uplo;
 typedef enum { TRI_NONUNIT = 0, TRI_UNIT = 1 } tri_diag;
 
 typedef enum {
-    TRI_F64 = 0,       /* FP64 storage, FP64 leaf recurrence and DFMA products            */
+    TRI_F64 = 0,       /* FP64 storage, FP64 leaf recurrence and DFMA products; small
+                          products split k over several CTAs and add the partial sums
+                          atomically, so results may differ between runs in the last
+                          bits                                                            */
     TRI_F32 = 1,       /* FP32 storage, FP32 leaf recurrence and FFMA products ("plain")  */
     TRI_F32_MIXED = 2  /* FP32 storage; split-BF16 tensor-core products with FP32
                           accumulation, then one Newton-Schulz step X <- X + X(I - TX)    */
@@ -154,6 +157,22 @@ TRI_API tri_status tri_batched_plan_destroy(tri_batched_plan *plan);
 TRI_API int tri_batched_plan_threads(const tri_batched_plan *plan);
 TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs,
                                    tri_uplo uplo, tri_diag diag, tri_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * tri_inv_host -- tri_inv on a matrix in HOST memory (the same in-place operation, the
+ * same split, Section 3 / Algorithm COMBRIT with beta = 2): the referenced triangle is
+ * copied to the device in 256-column panels (one 2-D copy each, about half of the n x n
+ * matrix), inverted with `dtype` on `stream`, and copied back the same way; the other
+ * triangle of the host matrix is neither read nor written.  Device memory for the matrix
+ * and the workspace comes from the stream-ordered pool and is released before return.
+ * Synchronises `stream` before returning (the host matrix holds the result on return).
+ * Page-locked host memory gives full link bandwidth; pageable memory also works.
+ * *bytes_moved (host pointer, may be NULL): bytes copied in both directions together.
+ * Errors: as tri_inv_ex; TRI_ERR_NOMEM if the device allocation fails; TRI_ERR_CUDA for
+ * a failed copy.  A zero pivot is reported by tri_get_info, as for tri_inv.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
+                                tri_dtype dtype, void *stream, int64_t *bytes_moved);
 
 /* ---------------------------------------------------------------------------------
  * Strided batch of equal-order triangular inverses, in place: matrix b starts at

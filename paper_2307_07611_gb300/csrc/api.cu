@@ -249,6 +249,58 @@ tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda
     return st;
 }
 
+// Host-memory form: the referenced triangle travels in 256-column panels (one 2-D copy
+// each), so about half of the n x n matrix crosses the host link in each direction.
+static int64_t host_panel_copies(bool upper, int64_t n, uint8_t *dev, int64_t ldd, uint8_t *host, int64_t ldh,
+                                 size_t es, cudaMemcpyKind kind, cudaStream_t s, cudaError_t *err) {
+    constexpr int64_t kPanel = 256;
+    int64_t bytes = 0;
+    for (int64_t j0 = 0; j0 < n && *err == cudaSuccess; j0 += kPanel) {
+        const int64_t cols = std::min(kPanel, n - j0);
+        const int64_t r0 = upper ? 0 : j0, rows = upper ? j0 + cols : n - j0;
+        uint8_t *d = dev + ((size_t)j0 * ldd + r0) * es, *h = host + ((size_t)j0 * ldh + r0) * es;
+        *err = kind == cudaMemcpyHostToDevice
+                   ? cudaMemcpy2DAsync(d, ldd * es, h, ldh * es, rows * es, cols, kind, s)
+                   : cudaMemcpy2DAsync(h, ldh * es, d, ldd * es, rows * es, cols, kind, s);
+        bytes += rows * cols * (int64_t)es;
+    }
+    return bytes;
+}
+
+tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, tri_dtype dtype,
+                        void *stream, int64_t *bytes_moved) {
+    if (bytes_moved) *bytes_moved = 0;
+    if (!valid_enums(uplo, diag, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(s, &c);
+    if (st != TRI_OK) return st;
+    const size_t es = dtype == TRI_F64 ? 8 : 4;
+    const int64_t ldd = (n + 31) / 32 * 32;
+    const size_t mat = ((size_t)ldd * n * es + 255) / 256 * 256;
+    const size_t need = tri_inv_workspace_size(n, dtype);
+    uint8_t *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, mat + need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    const bool upper = uplo == TRI_UPPER;
+    int64_t moved = host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyHostToDevice, s, &e);
+    if (e == cudaSuccess) {
+        st = tri_inv_ex(uplo, diag, n, buf, ldd, dtype, need ? buf + mat : nullptr, need, stream);
+        if (st == TRI_OK)
+            moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+    }
+    const cudaError_t ef = cudaFreeAsync(buf, s);
+    const cudaError_t es2 = cudaStreamSynchronize(s);
+    if (st == TRI_OK && (e != cudaSuccess || ef != cudaSuccess || es2 != cudaSuccess)) st = TRI_ERR_CUDA;
+    if (bytes_moved) *bytes_moved = moved;
+    return st;
+}
+
 size_t gen_inv_workspace_size(int64_t n, tri_dtype dtype) {
     if (n <= 0 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
     return gen_inv_ws_bytes(n, dtype);

@@ -45,6 +45,7 @@ def _declare(lib):
         "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
+        "tri_inv_host": ([i32, i32, i64, vp, i64, i32, vp, ctypes.POINTER(i64)], i32),
         "gen_inv": ([i64, vp, i64, i32, vp], i32),
         "tri_inv_strided_batched": ([i32, i32, i64, vp, i64, i64, i64, i32, vp], i32),
         "tri_inv_strided_batched_workspace_size": ([i64, i64, i32], sz),
@@ -193,6 +194,14 @@ def tri_inv_backward_strided_batched_ex(uplo, diag, n, x, ldx, sx, g, ldg, sg, d
 
 
 TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def tri_inv_host(uplo, diag, n, ptr, ld, dtype, stream=0):
+    """tri_inv on a matrix in host memory (ptr: host address).  Returns (status,
+    bytes copied in both directions); synchronises the stream."""
+    moved = ctypes.c_int64(0)
+    st = load().tri_inv_host(uplo, diag, n, ptr, ld, dtype, stream or None, ctypes.byref(moved))
+    return st, int(moved.value)
 
 
 def tri_inv_noalloc(uplo, diag, n, ptr, ld, dtype, stream=0) -> int:
