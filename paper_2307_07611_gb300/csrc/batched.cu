@@ -48,29 +48,66 @@ struct BLimits {
     static constexpr int kWTiles = (MAXT / 2) * (MAXT / 2); // W of the top level
 };
 
+// hi / mid / lo BF16 pieces of two values, packed as bf16x2 words.
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t &h, uint32_t &m, uint32_t &l) {
+    const __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(hh);
+    const float ra = a - hf.x, rb = b - hf.y;
+    const __nv_bfloat162 mm = __floats2bfloat162_rn(ra, rb);
+    const float2 mf = __bfloat1622float2(mm);
+    const __nv_bfloat162 ll = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+    h = *reinterpret_cast<const uint32_t *>(&hh);
+    m = *reinterpret_cast<const uint32_t *>(&mm);
+    l = *reinterpret_cast<const uint32_t *>(&ll);
+}
+
 // Writes the BF16 hi/mid/lo planes of the whole (nt*32)^2 block held in the tiles (the
 // strict upper part as zeros) at rows/columns row0 + ... of planes with leading dim ldp.
+// Lane = (row octet, column): each lane converts 8 consecutive rows of a column and
+// stores 16 bytes per plane (rows row0 + 8k are 16-byte aligned: ldp is a multiple of
+// 64 and the planes 256-byte aligned); octets that cross ntot or n are stored singly.
 template <typename T, int NT>
 __device__ __forceinline__ void write_planes(const T *tiles, int nt, int n, long long row0, long long ntot,
                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
                                              long long ldp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = NT / 32;
+    const int oct = lane & 3, cl = lane >> 2;
     for (int e = warp; e < nt * nt; e += nwarps) {
         const int I = e / nt, J = e % nt;
         const T *tp = I >= J ? tiles + (size_t)(I * (I + 1) / 2 + J) * TE : nullptr;
-#pragma unroll 4
-        for (int c = 0; c < 32; ++c) {
-            const long long gi = row0 + I * 32 + lane, gj = row0 + J * 32 + c;
-            if (gi >= ntot || gj >= ntot || I * 32 + lane >= n || J * 32 + c >= n) continue;
-            const float v = tp ? (float)tp[lane * TP + c] : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            const float r1 = v - __bfloat162float(h);
-            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const int rb = I * 32 + oct * 8;          // first row of the octet in the block
+        const long long gi = row0 + rb;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int c = cl + 8 * t, cj = J * 32 + c;
+            const long long gj = row0 + cj;
+            if (gj >= ntot || cj >= n || gi >= ntot || rb >= n) continue;
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = tp ? (float)tp[(oct * 8 + i) * TP + c] : 0.f;
             const long long o = gi + gj * ldp;
-            p0[o] = h;
-            p1[o] = m;
-            p2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            if (gi + 8 <= ntot && rb + 8 <= n) {
+                uint4 h, m, l;
+                split_pair(v[0], v[1], h.x, m.x, l.x);
+                split_pair(v[2], v[3], h.y, m.y, l.y);
+                split_pair(v[4], v[5], h.z, m.z, l.z);
+                split_pair(v[6], v[7], h.w, m.w, l.w);
+                *reinterpret_cast<uint4 *>(p0 + o) = h;
+                *reinterpret_cast<uint4 *>(p1 + o) = m;
+                *reinterpret_cast<uint4 *>(p2 + o) = l;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (gi + i >= ntot || rb + i >= n) continue;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
+                    const float r1 = v[i] - __bfloat162float(h);
+                    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                    p0[o + i] = h;
+                    p1[o + i] = m;
+                    p2[o + i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+                }
+            }
         }
     }
 }
@@ -89,12 +126,42 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     const long long ld = d.ld;
 
     // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
-    // One warp per tile, 32 independent loads in flight per lane.
+    // One warp per tile.  FP32 tiles that lie inside the block, from a 16-byte aligned
+    // source with ld a multiple of 4, come in as 8 float4 loads per lane (lane = 4
+    // consecutive elements along the contiguous index of the source); the rest as 32
+    // scalar loads per lane.
     const int ntl = nt * (nt + 1) / 2;
+    const bool vec_ok = sizeof(T) == 4 && (((uintptr_t)g & 15) == 0) && (ld % 4 == 0);
     for (int tl = warp; tl < ntl; tl += nwarps) {
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= tl) ++I;
         const int J = tl - I * (I + 1) / 2;
+        T *tp = tile_ptr(tiles, I, J);
+        if (vec_ok && I * 32 + 32 <= n) {
+            // contiguous index: rows (column-major source) or columns (transposed source)
+            const int q4 = (lane & 7) * 4, o8 = lane >> 3;
+            float4 v[8];
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const int other = o8 + 4 * s8;          // column (or row) of the tile
+                const int gi = TRANS ? I * 32 + other : I * 32 + q4;
+                const int gj = TRANS ? J * 32 + q4 : J * 32 + other;
+                v[s8] = *reinterpret_cast<const float4 *>(&g[vidx<TRANS>(gi, gj, ld)]);
+            }
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const int other = o8 + 4 * s8;
+                const float vv[4] = {v[s8].x, v[s8].y, v[s8].z, v[s8].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = TRANS ? other : q4 + q, c = TRANS ? q4 + q : other;
+                    T x = (T)vv[q];
+                    if (I == J) x = c > r ? T(0) : (c == r && UNIT ? T(1) : x);
+                    tp[r * TP + c] = x;
+                }
+            }
+            continue;
+        }
         T v[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -109,7 +176,6 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
                 v[q] = (gi == gj) ? T(1) : T(0);
             }
         }
-        T *tp = tile_ptr(tiles, I, J);
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             const int r = TRANS ? q : lane, c = TRANS ? lane : q;
@@ -131,13 +197,32 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             atomicMin(info, info_as >= 0 ? info_as : (row0 >= 0 ? (long long)(row0 + bad) : (long long)d.index));
     }
 
-    // Store the lower triangle back (unit diagonal not written), one warp per tile.
+    // Store the lower triangle back (unit diagonal not written), one warp per tile;
+    // off-diagonal tiles inside the block as float4 stores when the source allowed
+    // float4 loads.
     T *go = reinterpret_cast<T *>(d.ptr);
     for (int tl = warp; tl < ntl; tl += nwarps) {
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= tl) ++I;
         const int J = tl - I * (I + 1) / 2;
         const T *tp = tile_ptr(tiles, I, J);
+        if (vec_ok && I > J && I * 32 + 32 <= n) {
+            const int q4 = (lane & 7) * 4, o8 = lane >> 3;
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) {
+                const int other = o8 + 4 * s8;
+                float vv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = TRANS ? other : q4 + q, c = TRANS ? q4 + q : other;
+                    vv[q] = (float)tp[r * TP + c];
+                }
+                const int gi = TRANS ? I * 32 + other : I * 32 + q4;
+                const int gj = TRANS ? J * 32 + q4 : J * 32 + other;
+                *reinterpret_cast<float4 *>(&go[vidx<TRANS>(gi, gj, ld)]) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+            }
+            continue;
+        }
 #pragma unroll 8
         for (int q = 0; q < 32; ++q) {
             const int r = TRANS ? q : lane, c = TRANS ? lane : q;
