@@ -56,6 +56,37 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
     }
     if (i0 >= n || j0 >= n) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // Off-diagonal 64 x 64 tile inside the matrix, column-major source with 16-byte rows:
+    // thread t converts rows i0 + 8 (t % 8) .. + 7 of columns j0 + t / 8 and j0 + 32 + t / 8
+    // (two float4 loads, one 16-byte store per plane); a warp covers 4 whole columns.
+    if (!TRANS && !DIAG_ONLY && (i0 / 256) != (j0 / 256) && i0 + TS <= n && j0 + TS <= n &&
+        (((uintptr_t)a & 15) == 0) && (lda % 4) == 0 && (ldp % 8) == 0) {
+        const int t = threadIdx.x, r8 = (t & 7) * 8;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int64_t j = j0 + (t >> 3) + 32 * cc, i = i0 + r8;
+            const float4 u = *reinterpret_cast<const float4 *>(a + i + j * lda);
+            const float4 v = *reinterpret_cast<const float4 *>(a + i + 4 + j * lda);
+            const float x[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+            uint32_t hw[4], mw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                split3(x[2 * e], h0, m0, l0);
+                split3(x[2 * e + 1], h1, m1, l1);
+                const __nv_bfloat162 hp = __halves2bfloat162(h0, h1), mp = __halves2bfloat162(m0, m1),
+                                     lp = __halves2bfloat162(l0, l1);
+                hw[e] = *reinterpret_cast<const uint32_t *>(&hp);
+                mw[e] = *reinterpret_cast<const uint32_t *>(&mp);
+                lw[e] = *reinterpret_cast<const uint32_t *>(&lp);
+            }
+            const int64_t o = i + j * ldp;
+            *reinterpret_cast<uint4 *>(p0 + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(p1 + o) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+            *reinterpret_cast<uint4 *>(p2 + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        return;
+    }
     // Referenced triangle only; the rest reads as 0 and a unit diagonal as 1.
     auto fetch = [&](int64_t i, int64_t j) -> float {
         if (i >= n || j >= n || j > i) return 0.f;
