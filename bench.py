@@ -58,6 +58,21 @@ def flops_tri(n: int) -> float:
     return n ** 3 / 3.0
 
 
+def max_over_ranks(torch, dist, local_ms: float, world: int, device) -> float:
+    """Slowest rank's time: every rank contributes its own timed-region length (all_reduce
+    MAX over the process group; a single process returns its own)."""
+    t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world: int, flops_per_step: float, steps: int, max_ms: float) -> float:
+    """Whole-job throughput (TFLOP/s): the work of all ranks over the slowest rank's time
+    (replicas: every rank runs the same per-rank workload)."""
+    return world * flops_per_step * steps / (max_ms * 1e-3) / 1e12
+
+
 def dominant_traffic(kernel: str):
     """Per-launch DRAM bytes (read + write) of `kernel` from the committed ncu summary,
     or None if there is none or the kernel source changed since it was captured."""
@@ -411,12 +426,9 @@ def main():
     clk = clocks.stop()
 
     # max over ranks
-    tot = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    total_ms = float(tot.item())
+    total_ms = max_over_ranks(torch, dist, total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * flops_tri(n) * args.steps / (total_ms * 1e-3) / 1e12
+    value = aggregate_value(world, flops_tri(n), args.steps, total_ms)
 
     # quality of this mode's result (outside the timed region)
     def quality(code_):
@@ -508,12 +520,8 @@ def main():
             t0 = time.perf_counter()
             e2e_step()
             times.append(time.perf_counter() - t0)
-        ms = statistics.median(times) * 1e3
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        e2e = {"value": world * flops_tri(n) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+        ms = max_over_ranks(torch, dist, statistics.median(times) * 1e3, world, dev)
+        e2e = {"value": aggregate_value(world, flops_tri(n), 1, ms), "unit": "TFLOP/s",
                "h2d_bytes_per_step": moved // 2, "d2h_bytes_per_step": moved // 2,
                "ms_per_step": ms, "api": "tri_inv_host (pinned host matrix, wall clock, median)"}
 
