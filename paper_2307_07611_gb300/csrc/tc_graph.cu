@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -86,7 +87,8 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 // Bounded wait until region counter *f reaches EPI_WARPS.  False if this CTA or the
 // launch is aborting or the deadline passed (then it raises both abort words and the
 // device timeout word).
-__device__ bool wait_ready(const int *f, volatile int *abort_flag, int *abort_word, int *gtimeout) {
+__device__ bool wait_ready(const int *f, volatile int *abort_flag, int *abort_word, int *gtimeout,
+                           unsigned long long limit_ns) {
     if (ld_acquire(f) >= EPI_WARPS) return true;
     const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
@@ -97,7 +99,7 @@ __device__ bool wait_ready(const int *f, volatile int *abort_flag, int *abort_wo
                 *abort_flag = 1;
                 return false;
             }
-            if (gtimer() - t0 > kWaitLimitNs) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicExch(abort_word, 1);
                 atomicExch(gtimeout, 1);
@@ -188,7 +190,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
             }
             bool dok = true;
             for (int d = tl.dep0 + lane; d < tl.dep1 && dok; d += 32)
-                dok = wait_ready(ep.flags + deps[d], abort_flag, ep.abort_word, gtimeout);
+                dok = wait_ready(ep.flags + deps[d], abort_flag, ep.abort_word, gtimeout, ep.limit_ns);
             __syncwarp();
             ok = __all_sync(0xffffffffu, dok);
             if (!ok) break;
@@ -209,7 +211,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                         for (int kb = c0; kb < c1; ++kb) {
                             const int s = it % STAGES;
                             const uint32_t ph = (it / STAGES) & 1u;
-                            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, gtimeout)) {
+                            if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, gtimeout, ep.limit_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -244,7 +246,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                 for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb, ++lc) {
                     const int c1 = min(c0 + cb, tl.kb1);
                     const uint32_t a = lc & 1u, use = lc >> 1;
-                    if (!mbar_wait(tempty_bar(a), (use & 1u) ^ 1u, abort_flag, gtimeout)) {
+                    if (!mbar_wait(tempty_bar(a), (use & 1u) ^ 1u, abort_flag, gtimeout, ep.limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -255,7 +257,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                         for (int kb = c0; kb < c1; ++kb) {
                             const int s = it % STAGES;
                             const uint32_t ph = (it / STAGES) & 1u;
-                            if (!mbar_wait(full_bar(s), ph, abort_flag, gtimeout)) {
+                            if (!mbar_wait(full_bar(s), ph, abort_flag, gtimeout, ep.limit_ns)) {
                                 ok = false;
                                 break;
                             }
@@ -306,7 +308,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                 for (int i = 0; i < BN / 2; ++i) sum[i] = 0.f;
                 for (int c0 = tl.kb0; c0 < tl.kb1; c0 += cb, ++lc) {
                     const uint32_t a = lc & 1u, use = lc >> 1;
-                    if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
+                    if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout, ep.limit_ns)) {
                         ok = false;
                         break;
                     }
@@ -341,7 +343,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
             } else if (tl.op == G_UPD) {
                 if (tl.xin_flag >= 0) {
                     bool r = true;
-                    if (lane == 0) r = wait_ready(ep.flags + tl.xin_flag, abort_flag, ep.abort_word, gtimeout);
+                    if (lane == 0) r = wait_ready(ep.flags + tl.xin_flag, abort_flag, ep.abort_word, gtimeout, ep.limit_ns);
                     ok = __shfl_sync(0xffffffffu, r, 0);
                     __syncwarp();
                     if (!ok) break;
@@ -359,7 +361,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                         xo += xstep;
                     }
                 }
-                if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
+                if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout, ep.limit_ns)) {
                     ok = false;
                     break;
                 }
@@ -399,7 +401,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                 // hi / mid / lo pieces).
                 const uint32_t a = lc & 1u, use = lc >> 1;
                 ++lc;
-                if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout)) {
+                if (!mbar_wait(tfull_bar(a), use & 1u, abort_flag, gtimeout, ep.limit_ns)) {
                     ok = false;
                     break;
                 }
@@ -444,7 +446,7 @@ tc_graph_kernel(const __grid_constant__ GMaps maps, const GTile *__restrict__ ti
                 fence_proxy_async_global();
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) red_release_add(ep.flags + tl.out_flag, 1);
+                if (lane == 0 && tl.out_flag != ep.withhold) red_release_add(ep.flags + tl.out_flag, 1);
             }
             if (ep.timeline && warp == 2 && lane == 0) ep.timeline[(size_t)t * kTimelineWords + 5] = gtimer();
         }
@@ -815,6 +817,13 @@ cudaError_t launch_graph(const Ctx &c, bool trans, bool unit, int64_t n, const G
     if (e != cudaSuccess) return e;
     GEpi epl = ep;
     epl.timeline = nullptr;
+    // Failure-path test knobs (unset in normal use): TRI_DEBUG_WITHHOLD = a ready counter
+    // that is never published, TRI_DEBUG_WAIT_LIMIT_US = the deadline of every wait.
+    if (const char *w = std::getenv("TRI_DEBUG_WITHHOLD")) epl.withhold = std::atoi(w);
+    if (const char *l = std::getenv("TRI_DEBUG_WAIT_LIMIT_US")) {
+        const long long us = std::atoll(l);
+        if (us > 0) epl.limit_ns = (unsigned long long)us * 1000ull;
+    }
     if (trace_on()) {
         std::lock_guard<std::mutex> lk(g_tl_mu);
         Timeline &tl = g_timelines[std::make_pair(c.device, n)];

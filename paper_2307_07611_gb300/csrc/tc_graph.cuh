@@ -32,6 +32,10 @@ struct GEpi {
     int *flags;        // 3 * nrb * ncb ready counters (X, W, R), zeroed by launch_graph
     int *abort_word;   // flags[3 * nrb * ncb], zeroed with them
     unsigned long long *timeline;   // per-tile records while tracing (else null)
+    // Failure-path testing: the counter index whose publication is withheld (-1: none) and
+    // the deadline of every wait (ns).
+    int withhold = -1;
+    unsigned long long limit_ns = 4000000000ull;
 };
 
 // Per-tile timeline record written while tracing (list order, kTimelineWords words):

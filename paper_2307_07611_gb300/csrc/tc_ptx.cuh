@@ -66,14 +66,14 @@ static __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint3
 // Bounded wait.  Returns false if the CTA is aborting or the deadline passed (then it
 // raises the abort flag and the device timeout word).
 static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          int *gtimeout) {
+                                          int *gtimeout, unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 0) {
             if (*abort_flag) return false;
-            if (gtimer() - t0 > kWaitLimitNs) {
+            if (gtimer() - t0 > limit_ns) {
                 *abort_flag = 1;
                 atomicExch(gtimeout, 1);
                 return false;
