@@ -47,7 +47,8 @@ def parse():
                    help="skip the residual / oracle check (for profiler launch lists)")
     p.add_argument("--cpu-sample-stride", type=int, default=1)
     p.add_argument("--profile-config", default=None,
-                   choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512"],
+                   choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512",
+                            "combrit_beta"],
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
@@ -311,7 +312,7 @@ def _secondary_adjoint(torch, lib, dev, out, only):
     from paper_2307_07611_gb300 import inputs
     sh = int(torch.cuda.current_stream().cuda_stream)
     if only is not None and only != "adjoint_256x1024":
-        return out
+        return _secondary_combrit(torch, lib, dev, out, only)
 
     # differentiation: batch 256 of n = 1024 FP32 lower (uniform law), loss sum(W * T^-1)
     b, n = 256, 1024
@@ -331,6 +332,37 @@ def _secondary_adjoint(torch, lib, dev, out, only):
                      "unit": "TFLOP/s (n^3/3 forward, 4n^3/3 backward, per matrix)"}
     out["adjoint_256x1024"] = adj
     del pr, g, wk, dt
+    torch.cuda.empty_cache()
+    return _secondary_combrit(torch, lib, dev, out, only)
+
+
+def _secondary_combrit(torch, lib, dev, out, only):
+    """COMBRIT with beta = 2, 4, 8 blocks per level (the paper's comparison of block
+    counts, Table tab:combrit): FP64 n = 1024 (the paper's largest size, uniform law) and
+    FP32 n = 8192 (normal law), TFLOP/s by the n^3/3 convention."""
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    if only is not None and only != "combrit_beta":
+        return out
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    res = {}
+    for label, n, dt, law, tdt in (("f64_n1024", 1024, lib.TRI_F64, "uniform", torch.float64),
+                                   ("f32_n8192", 8192, lib.TRI_F32, "normal", torch.float32)):
+        t = inputs.tri_lower(n, seed=0, law=law)
+        pr = torch.from_numpy(np.ascontiguousarray(t.T)).to(tdt).to(dev)
+        wk = torch.empty_like(pr)
+        row = {}
+        for beta in (2, 4, 8):
+            ms = event_time(torch, lambda: lib.check(lib.tri_inv_combrit(0, 0, n, wk.data_ptr(), n, dt, beta, sh)),
+                            5, 2, setup=lambda: wk.copy_(pr))
+            row[f"beta{beta}"] = {"ms": ms, "value": n ** 3 / 3 / (ms * 1e-3) / 1e12}
+        ms = event_time(torch, lambda: lib.check(lib.tri_inv(0, 0, n, wk.data_ptr(), n, dt, sh)), 5, 2,
+                        setup=lambda: wk.copy_(pr))
+        row["tri_inv"] = {"ms": ms, "value": n ** 3 / 3 / (ms * 1e-3) / 1e12}
+        row["unit"] = "TFLOP/s (n^3/3)"
+        res[label] = row
+        del pr, wk
+    out["combrit_beta"] = res
     torch.cuda.empty_cache()
     return out
 

@@ -176,6 +176,9 @@ tri_status run_plain_levels(const Ctx &c, tri_dtype dt, bool trans, bool unit, i
 }
 
 size_t mixed_ws_bytes(int64_t n);
+size_t combrit_ws_bytes(int64_t n, tri_dtype dt, int beta);
+tri_status run_combrit(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a, int64_t lda, int beta,
+                       void *ws);
 size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt);
 tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws);
 tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws);
@@ -298,6 +301,27 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
     const cudaError_t es2 = cudaStreamSynchronize(s);
     if (st == TRI_OK && (e != cudaSuccess || ef != cudaSuccess || es2 != cudaSuccess)) st = TRI_ERR_CUDA;
     if (bytes_moved) *bytes_moved = moved;
+    return st;
+}
+
+tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, tri_dtype dtype,
+                           int beta, void *stream) {
+    if (!valid_enums(uplo, diag, dtype) || n < 0 || !(beta == 2 || beta == 4 || beta == 8)) return TRI_ERR_ARG;
+    if (dtype == TRI_F32_MIXED) return TRI_ERR_UNSUPPORTED;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(s, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = combrit_ws_bytes(n, dtype, beta);
+    void *ws = nullptr;
+    if (need > 0 && cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = run_combrit(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, beta, ws);
+    if (ws && cudaFreeAsync(ws, s) != cudaSuccess && st == TRI_OK) st = TRI_ERR_CUDA;
     return st;
 }
 

@@ -46,6 +46,7 @@ def _declare(lib):
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "tri_inv_host": ([i32, i32, i64, vp, i64, i32, vp, ctypes.POINTER(i64)], i32),
+        "tri_inv_combrit": ([i32, i32, i64, vp, i64, i32, i32, vp], i32),
         "gen_inv": ([i64, vp, i64, i32, vp], i32),
         "tri_inv_strided_batched": ([i32, i32, i64, vp, i64, i64, i64, i32, vp], i32),
         "tri_inv_strided_batched_workspace_size": ([i64, i64, i32], sz),
@@ -194,6 +195,11 @@ def tri_inv_backward_strided_batched_ex(uplo, diag, n, x, ldx, sx, g, ldg, sg, d
 
 
 TRI_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def tri_inv_combrit(uplo, diag, n, ptr, ld, dtype, beta, stream=0) -> int:
+    """tri_inv by COMBRIT with `beta` (2, 4, 8) diagonal blocks per level."""
+    return load().tri_inv_combrit(uplo, diag, n, ptr, ld, dtype, beta, stream or None)
 
 
 def tri_inv_host(uplo, diag, n, ptr, ld, dtype, stream=0):

@@ -43,7 +43,7 @@ def check_untouched(before, after, n, ld, lower, unit=False):
 
 
 def run_tri_inv(lib, torch, t, lower=True, unit=False, dtype="f32", ld_pad=3, stream=None,
-                mixed=False, workspace=False):
+                mixed=False, workspace=False, beta=None):
     """Invert the logical matrix t through the C ABI; returns (X, status) where X holds
     the referenced triangle (other triangle zero, unit diagonal set to 1)."""
     n = t.shape[0]
@@ -54,7 +54,10 @@ def run_tri_inv(lib, torch, t, lower=True, unit=False, dtype="f32", ld_pad=3, st
     dev = torch.from_numpy(host.copy()).cuda()
     s = stream or torch.cuda.current_stream()
     h = int(s.cuda_stream)
-    if workspace:
+    if beta is not None:
+        st = lib.tri_inv_combrit(lib.TRI_LOWER if lower else lib.TRI_UPPER,
+                                 lib.TRI_UNIT if unit else lib.TRI_NONUNIT, n, dev.data_ptr(), ld, code, beta, h)
+    elif workspace:
         need = lib.tri_inv_workspace_size(n, code)
         ws = torch.empty(max(need, 1) + 256, dtype=torch.uint8, device="cuda")
         ptr = (ws.data_ptr() + 255) // 256 * 256

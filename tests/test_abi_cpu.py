@@ -136,3 +136,14 @@ def test_mixed_schedule_small_grids_and_errors(libtri):
         lib.tri_mixed_schedule_stats(256, 152)      # no tensor-core part
     with pytest.raises(lib.TriError):
         lib.tri_mixed_schedule_stats(4096, 0)
+
+
+def test_combrit_argument_errors_need_no_gpu(libtri):
+    A = lib.TRI_ERR_ARG
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 3) == A          # beta not 2/4/8
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 16) == A
+    assert lib.tri_inv_combrit(0, 0, -1, 4096, 16, lib.TRI_F32, 4) == A
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32_MIXED, 4) == lib.TRI_ERR_UNSUPPORTED
+    assert lib.tri_inv_combrit(0, 0, 0, 0, 1, lib.TRI_F64, 8) == lib.TRI_OK       # n == 0: no-op
+    assert lib.tri_inv_combrit(0, 0, 16, 0, 16, lib.TRI_F32, 2) == A             # NULL
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 15, lib.TRI_F32, 2) == A          # lda < n
