@@ -7,8 +7,8 @@ never does, and this package imports nothing from it.
 Two layers:
 
 * ``oracle.c`` (compiled here with gcc): the column recurrence of CRIT (Section 4.2),
-  Crout LU in SKUL's row order (Section 5.1), A^-1 = U^-1 L^-1 and the adjoint
-  dT = -P(X^T G X^T).  Plain loops in binary64, no fast-math, no FMA contraction.
+  Crout LU in SKUL's row order (Section 5.1), A^-1 = U^-1 L^-1, Algorithms SKUL and SQR
+  as printed (Section 5.1) and the adjoint dT = -P(X^T G X^T).  Plain loops in binary64, no fast-math, no FMA contraction.
 * Pure-Python pieces for tiny sizes: the Hopscotch series H(a, b) (Definition 3.1,
   Example "H(1,5)"), the combinatorial entry formula of the main Theorem of Section 3
   (Eq. "TMatrixInversecombinatorixFormula") and an instrumented CRIT* that counts its
@@ -65,6 +65,10 @@ def _load():
         lib.oracle_crout.restype = i64
         lib.oracle_gen_inv.argtypes = [i64, dp, i64, dp, i64, i32]
         lib.oracle_gen_inv.restype = i64
+        lib.oracle_skul.argtypes = [i64, dp, i64, dp, dp, dp, dp]
+        lib.oracle_skul.restype = i64
+        lib.oracle_sqr.argtypes = [i64, dp, i64, dp, dp, dp]
+        lib.oracle_sqr.restype = i64
         lib.oracle_tri_grad.argtypes = [i32, i32, i64, dp, i64, dp, i64, dp, i64, i32]
         lib.oracle_tri_grad.restype = None
         lib.oracle_max_threads.argtypes = []
@@ -133,6 +137,28 @@ def crout(a, threads: int = 0):
     if n:
         _check(_load().oracle_crout(n, ac.ctypes.data, n, lo.ctypes.data, up.ctypes.data, threads))
     return np.ascontiguousarray(lo), np.ascontiguousarray(up)
+
+
+def skul(a):
+    """Algorithm SKUL (Section 5.1): returns (L, U, S, K) with A = L U (L lower, U unit
+    upper), S = U^-1, K = L^-1, so A^-1 = S K.  Sequential, FP64."""
+    ac = _f64_colmajor(a)
+    n = ac.shape[0]
+    outs = [np.zeros((n, n), order="F") for _ in range(4)]
+    if n:
+        _check(_load().oracle_skul(n, ac.ctypes.data, n, *[o.ctypes.data for o in outs]))
+    return tuple(np.ascontiguousarray(o) for o in outs)
+
+
+def sqr(a):
+    """Algorithm SQR (Section 5.1): returns (Q, R, S) with A = Q R by modified
+    Gram-Schmidt and S = R^-1, so A^-1 = S Q^T.  Sequential, FP64."""
+    ac = _f64_colmajor(a)
+    n = ac.shape[0]
+    outs = [np.zeros((n, n), order="F") for _ in range(3)]
+    if n:
+        _check(_load().oracle_sqr(n, ac.ctypes.data, n, *[o.ctypes.data for o in outs]))
+    return tuple(np.ascontiguousarray(o) for o in outs)
 
 
 def gen_inv(a, threads: int = 0) -> np.ndarray:

@@ -26,6 +26,11 @@
  *                        (Section 5.1, Algorithm "SKUL"): A = L U.
  *   oracle_gen_inv       A^-1 = U^-1 L^-1 from oracle_crout and oracle_tri_inv
  *                        (SKUL: "S K = A^-1"; BRSI with two blocks, Section 5.2).
+ *   oracle_skul          Algorithm SKUL (Section 5.1) as printed: Crout L, U with the
+ *                        inverse factors K = L^-1 (rows) and S = U^-1 (columns) built
+ *                        alongside; A^-1 = S K.
+ *   oracle_sqr           Algorithm SQR (Section 5.1): modified Gram-Schmidt A = Q R with
+ *                        S = R^-1 built column by column; A^-1 = S Q^T.
  *   oracle_tri_grad      adjoint of X = T^-1 for a loss with cotangent G:
  *                        dT = -P(X^T G X^T), P the projection on T's free entries.
  *                        (Not in the paper; the plain definition from d(T^-1) =
@@ -270,4 +275,119 @@ void oracle_tri_grad(int upper, int unit, int64_t n, const double *X, int64_t ld
     }
     free(M);
     free(Xr);
+}
+
+/* Algorithm SKUL (Section 5.1), step by step in the paper's order, 0-based:
+ *   L_{i,0} = A_{i,0};  U_ii = S_ii = K_ii = 1;  U_{0,j} = A_{0,j} / L_00;  D_00 = 1/L_00;
+ *   for i = 1 .. n-1:
+ *     L_ij = A_ij - sum_{p<j} L_ip U_pj                          (1 <= j <= i)
+ *     D_ii = 1 / L_ii
+ *     K_ij = -(sum_{p=j}^{i-1} L_ip K_pj) D_ii                   (j < i; unit-diagonal K)
+ *     U_ij = (A_ij - sum_{p<i} L_ip U_pj) / L_ii                 (j > i)
+ *     S_{l,i+1} = -sum_{p=l}^{i} S_lp U_{p,i+1}                  (l <= i, when i < n-1)
+ *   (S_{0,1} = -U_{0,1} is the i = 0 case of the last line.)  Finally K <- K D.
+ * The row of K is the CRIT recurrence on L run as each row of L appears, and the column
+ * of S the CRIT* recurrence on U run as each column of U is complete.
+ * Outputs: L, U, S, K full n x n column-major (ld n), zero outside their triangles.
+ * Returns -1, the first row whose pivot L_ii is zero or non-finite, or -2 (no memory). */
+int64_t oracle_skul(int64_t n, const double *A, int64_t lda, double *L, double *U, double *S, double *K) {
+    if (n <= 0) return -1;
+    memset(L, 0, sizeof(double) * (size_t)(n * n));
+    memset(U, 0, sizeof(double) * (size_t)(n * n));
+    memset(S, 0, sizeof(double) * (size_t)(n * n));
+    memset(K, 0, sizeof(double) * (size_t)(n * n));
+    double *D = (double *)calloc((size_t)n, sizeof(double));
+    if (!D) return -2;
+    int64_t bad = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        AT(L, n, i, 0) = AT(A, lda, i, 0);
+        AT(U, n, i, i) = 1.0;
+        AT(S, n, i, i) = 1.0;
+        AT(K, n, i, i) = 1.0;
+    }
+    double l00 = AT(L, n, 0, 0);
+    if (l00 == 0.0 || !isfinite(l00)) { free(D); return 0; }
+    for (int64_t j = 1; j < n; ++j) AT(U, n, 0, j) = AT(A, lda, 0, j) / l00;
+    D[0] = 1.0 / l00;
+    if (n > 1) AT(S, n, 0, 1) = -AT(U, n, 0, 1);
+    for (int64_t i = 1; i < n && bad < 0; ++i) {
+        for (int64_t j = 1; j <= i; ++j) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < j; ++p) acc += AT(L, n, i, p) * AT(U, n, p, j);
+            AT(L, n, i, j) = AT(A, lda, i, j) - acc;
+        }
+        const double lii = AT(L, n, i, i);
+        if (lii == 0.0 || !isfinite(lii)) { bad = i; break; }
+        D[i] = 1.0 / lii;
+        for (int64_t j = 0; j < i; ++j) {
+            double acc = 0.0;
+            for (int64_t p = j; p < i; ++p) acc += AT(L, n, i, p) * AT(K, n, p, j);
+            AT(K, n, i, j) = -acc * D[i];
+        }
+        for (int64_t j = i + 1; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t p = 0; p < i; ++p) acc += AT(L, n, i, p) * AT(U, n, p, j);
+            AT(U, n, i, j) = (AT(A, lda, i, j) - acc) / lii;
+        }
+        if (i < n - 1)
+            for (int64_t l = 0; l <= i; ++l) {
+                double acc = 0.0;
+                for (int64_t p = l; p <= i; ++p) acc += AT(S, n, l, p) * AT(U, n, p, i + 1);
+                AT(S, n, l, i + 1) = -acc;
+            }
+    }
+    if (bad < 0)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = j; i < n; ++i) AT(K, n, i, j) *= D[j];
+    free(D);
+    return bad;
+}
+
+/* Algorithm SQR (Section 5.1): modified Gram-Schmidt QR of A with S = R^-1 built one
+ * column at a time as the columns of R appear.  0-based, for j = 0 .. n-1:
+ *     qh = a_j;  for i < j:  R_ij = qh . q_i;  qh <- qh - R_ij q_i     (MGS)
+ *     R_jj = ||qh||_2  (stop if zero);  D_jj = 1/R_jj;  q_j = D_jj qh;  S_jj = 1
+ *     S_ij = -(1/R_jj) sum_{p=i}^{j-1} S_ip R_pj                         (i < j)
+ *   and finally S <- D S, so that A = Q R and A^-1 = S Q^T.
+ * The printed algorithm lists the S update before R_jj although it divides by R_jj; the
+ * update is taken after R_jj here.  Outputs full n x n column-major (ld n); Q
+ * orthonormal, R and S upper.  Returns -1, the first column j with R_jj zero or
+ * non-finite, or -2. */
+int64_t oracle_sqr(int64_t n, const double *A, int64_t lda, double *Q, double *R, double *S) {
+    if (n <= 0) return -1;
+    memset(Q, 0, sizeof(double) * (size_t)(n * n));
+    memset(R, 0, sizeof(double) * (size_t)(n * n));
+    memset(S, 0, sizeof(double) * (size_t)(n * n));
+    double *qh = (double *)malloc(sizeof(double) * (size_t)n);
+    double *D = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!qh || !D) { free(qh); free(D); return -2; }
+    int64_t bad = -1;
+    for (int64_t j = 0; j < n && bad < 0; ++j) {
+        for (int64_t r = 0; r < n; ++r) qh[r] = AT(A, lda, r, j);
+        for (int64_t i = 0; i < j; ++i) {
+            double dot = 0.0;
+            for (int64_t r = 0; r < n; ++r) dot += qh[r] * AT(Q, n, r, i);
+            AT(R, n, i, j) = dot;
+            for (int64_t r = 0; r < n; ++r) qh[r] -= dot * AT(Q, n, r, i);
+        }
+        double ss = 0.0;
+        for (int64_t r = 0; r < n; ++r) ss += qh[r] * qh[r];
+        const double rjj = sqrt(ss);
+        if (rjj == 0.0 || !isfinite(rjj)) { bad = j; break; }
+        AT(R, n, j, j) = rjj;
+        D[j] = 1.0 / rjj;
+        for (int64_t r = 0; r < n; ++r) AT(Q, n, r, j) = D[j] * qh[r];
+        AT(S, n, j, j) = 1.0;
+        for (int64_t i = 0; i < j; ++i) {
+            double acc = 0.0;
+            for (int64_t p = i; p < j; ++p) acc += AT(S, n, i, p) * AT(R, n, p, j);
+            AT(S, n, i, j) = -acc / rjj;
+        }
+    }
+    if (bad < 0)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i <= j; ++i) AT(S, n, i, j) *= D[i];
+    free(qh);
+    free(D);
+    return bad;
 }

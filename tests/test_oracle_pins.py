@@ -242,6 +242,85 @@ def test_sqr_printed_r_inverse():
     assert np.abs(oracle.tri_inv(g["R"], lower=False) - g["S_R"]).max() < 1.5e-4
 
 
+def test_skul_algorithm_printed_example():
+    # Algorithm SKUL run as printed reproduces the four factors of the example (Section 6.1)
+    g = matrices("skul_sqr_5x5.txt")
+    lo, up, s, k = oracle.skul(g["A"])
+    for name, got in (("L", lo), ("U", up), ("S", s), ("K", k)):
+        assert np.abs(got - g[name]).max() < 1.5e-4, name
+
+
+def test_sqr_algorithm_printed_example():
+    # Algorithm SQR reproduces the printed Q, R and S = R^-1 (Section 6.1); the printed A
+    # carries 4 decimals, so R (entries up to 4.8) agrees to about 1.5e-4.
+    g = matrices("skul_sqr_5x5.txt")
+    q, r, s = oracle.sqr(g["A"])
+    assert np.abs(q - g["Q"]).max() < 1.5e-4
+    assert np.abs(r - g["R"]).max() < 2e-4
+    assert np.abs(s - g["S_R"]).max() < 1.5e-4
+
+
+@pytest.mark.parametrize("n", [1, 2, 9, 70])
+def test_skul_factors_invariants(n):
+    a = inputs.general(n, seed=40 + n, dtype=np.float64)
+    lo, up, s, k = oracle.skul(a)
+    assert np.abs(lo @ up - a).max() < 1e-13 * max(1.0, np.abs(a).max())
+    assert not np.any(np.triu(lo, 1)) and not np.any(np.tril(up, -1))
+    assert not np.any(np.tril(s, -1)) and not np.any(np.triu(k, 1))
+    assert np.array_equal(np.diag(up), np.ones(n)) and np.array_equal(np.diag(s), np.ones(n))
+    eye = np.eye(n)
+    # S = U^-1 and K = L^-1 against LAPACK's triangular solves
+    assert np.abs(s - sla.solve_triangular(up, eye, lower=False, unit_diagonal=True)).max() < 1e-13
+    want_k = sla.solve_triangular(lo, eye, lower=True)
+    assert np.abs(k - want_k).max() <= 1e-13 * np.abs(want_k).max()
+    want = np.linalg.inv(a)
+    assert np.abs(s @ k - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_skul_singular_pivot():
+    # the leading 2 x 2 block is singular: L_11 = 4 - 2 * 2 = 0 exactly, so SKUL stops at
+    # row 1 (the algorithm's "stop" on a zero pivot)
+    a = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 7.0], [1.0, 1.0, 1.0]])
+    with pytest.raises(oracle.SingularError) as e:
+        oracle.skul(a)
+    assert e.value.index == 1
+    with pytest.raises(oracle.SingularError) as e:
+        oracle.skul(np.zeros((3, 3)))
+    assert e.value.index == 0
+
+
+@pytest.mark.parametrize("n", [1, 3, 16, 64])
+def test_sqr_factors_invariants(n):
+    a = inputs.general(n, seed=80 + n, dtype=np.float64)
+    q, r, s = oracle.sqr(a)
+    eye = np.eye(n)
+    assert np.abs(q @ r - a).max() < 1e-13 * max(1.0, np.abs(a).max())
+    assert np.abs(q.T @ q - eye).max() < 1e-12
+    assert not np.any(np.tril(r, -1)) and np.all(np.diag(r) > 0)
+    # the QR with a positive diagonal is unique: LAPACK's Householder QR, signs fixed
+    qh, rh = np.linalg.qr(a)
+    sg = np.sign(np.diag(rh))
+    assert np.abs(q - qh * sg).max() < 1e-11
+    assert np.abs(r - sg[:, None] * rh).max() < 1e-11 * np.abs(rh).max()
+    assert np.abs(s - sla.solve_triangular(r, eye, lower=False)).max() < 1e-12 * np.abs(s).max()
+    want = np.linalg.inv(a)
+    assert np.abs(s @ q.T - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_sqr_rank_deficient_column():
+    a = np.random.default_rng(5).standard_normal((4, 4))
+    a[:, 2] = 2.0 * a[:, 0] - a[:, 1]    # column 2 in the span of columns 0 and 1
+    with pytest.raises(oracle.SingularError):
+        oracle.sqr(np.zeros((3, 3)))
+    q, r, s = None, None, None
+    try:
+        q, r, s = oracle.sqr(a)
+    except oracle.SingularError as e:
+        assert e.index == 2
+    else:                                 # rounding may leave a tiny nonzero R_22
+        assert abs(r[2, 2]) < 1e-12 * np.abs(r).max()
+
+
 @pytest.mark.parametrize("n", [1, 7, 120])
 def test_gen_inv_matches_lapack(n):
     a = inputs.general(n, seed=n, dtype=np.float64)
