@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--cpu-sample-stride", type=int, default=1)
     p.add_argument("--profile-config", default=None,
                    choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512",
-                            "combrit_beta"],
+                            "combrit_beta", "factor_f32_n16384"],
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
@@ -343,7 +343,7 @@ def _secondary_combrit(torch, lib, dev, out, only):
     import numpy as np
     from paper_2307_07611_gb300 import inputs
     if only is not None and only != "combrit_beta":
-        return out
+        return _secondary_factor(torch, lib, dev, out, only)
     sh = int(torch.cuda.current_stream().cuda_stream)
     res = {}
     for label, n, dt, law, tdt in (("f64_n1024", 1024, lib.TRI_F64, "uniform", torch.float64),
@@ -363,6 +363,64 @@ def _secondary_combrit(torch, lib, dev, out, only):
         res[label] = row
         del pr, wk
     out["combrit_beta"] = res
+    torch.cuda.empty_cache()
+    return _secondary_factor(torch, lib, dev, out, only)
+
+
+def _secondary_factor(torch, lib, dev, out, only):
+    """Inverse factorisations (Section 5.1) on the general FP32 n = 16384 workload:
+    SKUL (A = L U with K = L^-1, S = U^-1; executed flops 2n^3/3 + 2n^3/3) and SQR
+    (A = Q R with S = R^-1)."""
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    if only is not None and only != "factor_f32_n16384":
+        return out
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    n = 16384
+    a = inputs.general(n, seed=0, dtype=np.float32)
+    pr = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
+    wk = torch.empty_like(pr)
+    sk = torch.empty_like(pr)
+    res = {}
+    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32)):
+        need = lib.skul_workspace_size(n, code)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        ms = event_time(torch, lambda: lib.check(lib.skul_ex(n, wk.data_ptr(), n, sk.data_ptr(), n, code, wp, need,
+                                                             sh)), 2 if name == "mixed" else 1, 1,
+                        setup=lambda: wk.copy_(pr))
+        # ||L U - A|| on a sample of columns: column c of L U is L[:, :c+1] U[:c+1, c]
+        cols = [0, 8191, 16383]
+        lu = wk.T
+        errs = []
+        for c in cols:
+            col = torch.tril(lu[:, :c + 1]).double() @ torch.cat(
+                [lu[:c, c].double(), torch.ones(1, dtype=torch.float64, device=dev)])
+            ac = pr.T[:, c].double()
+            errs.append(float((col - ac).norm() / ac.norm()))
+        res[name] = {"ms": ms, "value": 4 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "lu_column_err_max": max(errs)}
+        del ws
+    res["unit"] = "TFLOP/s (4n^3/3 executed: LU plus both inverse factors)"
+    out["skul_f32_n16384"] = res
+    # SQR: A = Q R with S = R^-1 (value by the MGS count 2n^3 + n^3/3 for S; the block
+    # Gram-Schmidt re-orthogonalisation executes 2n^3 more)
+    rr = torch.empty_like(pr)
+    res = {}
+    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32)):
+        need = lib.sqr_workspace_size(n, code)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        ms = event_time(torch, lambda: lib.check(lib.sqr_ex(n, wk.data_ptr(), n, rr.data_ptr(), n, sk.data_ptr(), n,
+                                                            code, wp, need, sh)), 2 if name == "mixed" else 1, 1,
+                        setup=lambda: wk.copy_(pr))
+        cols = [0, 8191, 16383]
+        q = wk[cols, :].double()                         # rows of the buffer = columns of Q
+        orth = float((q @ q.T - torch.eye(len(cols), dtype=torch.float64, device=dev)).abs().max())
+        res[name] = {"ms": ms, "value": 7 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "sampled_orthogonality": orth}
+        del ws
+    res["unit"] = "TFLOP/s (7n^3/3: MGS QR 2n^3 plus S n^3/3)"
+    out["sqr_f32_n16384"] = res
+    del pr, wk, sk, rr
     torch.cuda.empty_cache()
     return out
 

@@ -125,6 +125,68 @@ TRI_API tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, 
                               size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * SKUL (Algorithm SKUL, Section 5.1): the unpivoted Crout factorisation A = L U together
+ * with the inverse factors K = L^-1 and S = U^-1, so that A^-1 = S K, for preconditioners
+ * that want the direct and the inverse factors at once.  Computed block-recursively as in
+ * gen_inv (the factors are kept instead of multiplied out), then put in Crout form.
+ *   n     order, 0 <= n <= 65535.
+ *   a     device, lda x n column-major, lda >= n.  In: A.  Out: L on and below the
+ *         diagonal (non-unit), U strictly above it (its unit diagonal is not stored).
+ *   sk    device, ldsk x n column-major, ldsk >= n, not overlapping a.  Out only: K on
+ *         and below the diagonal, S strictly above it (unit diagonal not stored).
+ *   dtype TRI_F64, TRI_F32 or TRI_F32_MIXED (as gen_inv).
+ * Same pivot rule as gen_inv: no pivoting, a zero or non-finite pivot is reported by
+ * tri_get_info (its factors are then not meaningful).
+ * Errors: TRI_ERR_ARG (bad enum, n < 0, null pointers, small leading dimensions, a == sk),
+ *         TRI_ERR_UNSUPPORTED (n > 65535), TRI_ERR_NOMEM, TRI_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status skul(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype,
+                        void *stream);
+
+/* Bytes of 256-byte aligned device scratch skul_ex needs (the product temporaries of the
+ * recursion, the BF16 planes for TRI_F32_MIXED and n elements for the pivots). */
+TRI_API size_t skul_workspace_size(int64_t n, tri_dtype dtype);
+
+/* skul with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+TRI_API tri_status skul_ex(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * SQR (Algorithm SQR, Section 5.1): A = Q R (Q orthonormal, R upper with a positive
+ * diagonal) together with S = R^-1, so that A^-1 = S Q^T.  No pivoting is needed: any
+ * non-singular A whose column blocks are not too ill-conditioned (see below) factors.
+ * Built over blocks of columns (recursive block Gram-Schmidt with one
+ * re-orthogonalisation, S formed as each block column of R completes; leaves of 64
+ * columns, 32 in FP64, by Cholesky QR run twice).
+ *   n     order, 0 <= n <= 65535.
+ *   a     device, lda x n column-major, lda >= n.  In: A.  Out: Q.
+ *   r, s  device, ldr / lds x n column-major (>= n), out only: R and S = R^-1 on and
+ *         above the diagonal, zero below.  a, r and s must not overlap.
+ *   dtype TRI_F64, TRI_F32 or TRI_F32_MIXED (the block products Q1^T A2, Q1 R12, S11 R12
+ *         S22 on the tensor cores with three-term split BF16, where they are large).
+ * A column j whose leaf Gram matrix has a pivot that is not positive and finite (A
+ * singular, or a leaf block with condition number beyond about u^-1/2) is reported by
+ * tri_get_info as index j; the factors are then not meaningful.
+ * Errors: TRI_ERR_ARG (bad enum, n < 0, null pointers, small leading dimensions,
+ *         overlapping buffers), TRI_ERR_UNSUPPORTED (n > 65535), TRI_ERR_NOMEM,
+ *         TRI_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds,
+                       tri_dtype dtype, void *stream);
+
+/* Bytes of 256-byte aligned device scratch sqr_ex needs. */
+TRI_API size_t sqr_workspace_size(int64_t n, tri_dtype dtype);
+
+/* sqr with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+TRI_API tri_status sqr_ex(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds,
+                          tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
+
+/* General inverse through SQR, in place: A <- A^-1 = S Q^T (Section 5.1, "S Q^t =
+ * A^-1").  Same arguments, conditions and errors as gen_inv; scratch (about 3 n^2
+ * elements, plus BF16 planes for TRI_F32_MIXED) is allocated on the stream. */
+TRI_API tri_status sqr_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * Batched triangular inverses of uneven sizes, in place (block-Jacobi preconditioners):
  * every block is inverted by the recursive split (Section 4.1, block count 2) with CRIT
  * leaves (Section 4.2), entirely in shared memory, inside ONE persistent kernel whose

@@ -181,6 +181,13 @@ tri_status run_combrit(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_
                        void *ws);
 size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt);
 tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws);
+size_t skul_ws_bytes(int64_t n, tri_dtype dt);
+tri_status run_skul(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, void *ws);
+size_t sqr_ws_bytes(int64_t n, tri_dtype dt);
+tri_status run_sqr(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s,
+                   int64_t lds, void *ws);
+size_t sqr_inv_ws_bytes(int64_t n, tri_dtype dt);
+tri_status run_sqr_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws);
 tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws);
 
 }  // namespace triinv
@@ -360,6 +367,117 @@ tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *strea
     }
     st = gen_inv_ex(n, a, lda, dtype, ws, need, stream);
     cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
+    return st;
+}
+
+size_t skul_workspace_size(int64_t n, tri_dtype dtype) {
+    if (n <= 0 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
+    return skul_ws_bytes(n, dtype);
+}
+
+tri_status skul_ex(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype, void *workspace,
+                   size_t ws_bytes, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || !sk || lda < n || ldsk < n || a == sk) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    const size_t need = skul_ws_bytes(n, dtype);
+    if (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)) return TRI_ERR_NOMEM;
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    return run_skul(c, dtype, n, a, lda, sk, ldsk, workspace);
+}
+
+tri_status skul(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || !sk || lda < n || ldsk < n || a == sk) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(s, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = skul_ws_bytes(n, dtype);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = skul_ex(n, a, lda, sk, ldsk, dtype, ws, need, stream);
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
+    return st;
+}
+
+size_t sqr_workspace_size(int64_t n, tri_dtype dtype) {
+    if (n <= 0 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
+    return sqr_ws_bytes(n, dtype);
+}
+
+static bool overlaps(const void *p, int64_t ldp, const void *q, int64_t ldq, int64_t n, size_t es) {
+    const uint8_t *a0 = (const uint8_t *)p, *a1 = a0 + ((size_t)(n - 1) * ldp + n) * es;
+    const uint8_t *b0 = (const uint8_t *)q, *b1 = b0 + ((size_t)(n - 1) * ldq + n) * es;
+    return a0 < b1 && b0 < a1;
+}
+
+tri_status sqr_ex(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds, tri_dtype dtype,
+                  void *workspace, size_t ws_bytes, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || !r || !s || lda < n || ldr < n || lds < n) return TRI_ERR_ARG;
+    const size_t es = dtype == TRI_F64 ? 8 : 4;
+    if (overlaps(a, lda, r, ldr, n, es) || overlaps(a, lda, s, lds, n, es) || overlaps(r, ldr, s, lds, n, es))
+        return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    const size_t need = sqr_ws_bytes(n, dtype);
+    if (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)) return TRI_ERR_NOMEM;
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    return run_sqr(c, dtype, n, a, lda, r, ldr, s, lds, workspace);
+}
+
+tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds, tri_dtype dtype,
+               void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    cudaStream_t st_ = (cudaStream_t)stream;
+    if (!a || !r || !s || lda < n || ldr < n || lds < n) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    Ctx c;
+    tri_status st = device_ctx(st_, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = sqr_ws_bytes(n, dtype);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, need, st_) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = sqr_ex(n, a, lda, r, ldr, s, lds, dtype, ws, need, stream);
+    cudaError_t e = cudaFreeAsync(ws, st_);
+    if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
+    return st;
+}
+
+tri_status sqr_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < n) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    cudaStream_t st_ = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(st_, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = sqr_inv_ws_bytes(n, dtype);
+    void *ws = nullptr;
+    if (cudaMallocAsync(&ws, need, st_) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = run_sqr_inv(c, dtype, n, a, lda, ws);
+    cudaError_t e = cudaFreeAsync(ws, st_);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
 }

@@ -33,6 +33,9 @@ struct GemmArgs {
     int64_t sa = 0, sb = 0, sc = 0;           // these strides (elements)
     int64_t batch2 = 1;                       // an outer batch level (product index =
     int64_t sa2 = 0, sb2 = 0, sc2 = 0;        // inner + batch * outer)
+    bool split_k = false;                     // FP32 on CUDA cores: allow splitting a long
+                                              // k over CTAs (atomic adds, beta == 0 only;
+                                              // FP64 always may)
 };
 
 double gemm_flops(const GemmArgs &g);

@@ -30,9 +30,11 @@ namespace {
 // then K = L^-1 (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
 // The two triangular inverses run on the tiled in-shared-memory split (tile_inverse.cuh):
 // L (unit diagonal) and U^T are copied into 32 x 32 tiles and inverted there.
+// lu_out (may be null, else the same matrix as a): the packed Doolittle factors of the
+// block are written back over it (L strictly below the diagonal, U on and above it).
 template <typename T, int L, int NT>
-__global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *__restrict__ a, int64_t lda, T *__restrict__ ks,
-                                                     int64_t ldk, int64_t off, int nb, long long *info) {
+__global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T *__restrict__ ks, int64_t ldk,
+                                                     int64_t off, int nb, long long *info, T *lu_out) {
     constexpr int NTL = L / 32;                         // tile rows
     constexpr int KT = NTL * (NTL + 1) / 2;             // lower tiles
     constexpr int WT = (NTL / 2) * (NTL / 2) > 0 ? (NTL / 2) * (NTL / 2) : 1;
@@ -118,6 +120,11 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *__restrict__ a, in
             for (int c = 0; c < CW; ++c) s[rg * 8 + r][cg * CW + c] = v[r][c];
         __syncthreads();
     }
+    if (lu_out)
+        for (int idx = tid; idx < nb * nb; idx += NT) {
+            const int i = idx % nb, j = idx / nb;
+            lu_out[(off + i) + (off + j) * lda] = s[i][j];
+        }
     const int nt = (nb + 31) / 32;
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0: lower view = L (unit diagonal); pass 1: lower view = U^T.
@@ -204,12 +211,13 @@ struct GenLayout {
     std::vector<size_t> depth_off;
 };
 
-GenLayout gen_layout(int64_t n, tri_dtype dt) {
+// with_ks: the K\S buffer lives in the scratch (gen_inv); SKUL writes it to the caller's.
+GenLayout gen_layout(int64_t n, tri_dtype dt, bool with_ks = true) {
     GenLayout g{};
     const int L = leaf_size(dt);
     std::vector<int64_t> sz;
     depth_sizes(n, L, sz);
-    g.ks = al((size_t)n * n * esz(dt));
+    g.ks = with_ks ? al((size_t)n * n * esz(dt)) : 0;
     size_t o = g.ks;
     for (int64_t s : sz) {
         g.depth_off.push_back(o);
@@ -228,6 +236,7 @@ struct GenCtx {
     uint8_t *ws;
     GenLayout lay;
     int L;
+    bool keep = false;   // write L21, U12 and the leaf factors back over A (SKUL)
 };
 
 constexpr int64_t kTcMin = 512;   // smaller products stay on CUDA cores
@@ -248,7 +257,8 @@ cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int6
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         lu_leaf_kernel<double, L, NT><<<1, NT, sm, g.c->stream>>>((const double *)a, lda, (double *)ks, ldk,
-                                                                  off, nb, g.c->info);
+                                                                  off, nb, g.c->info,
+                                                                  g.keep ? (double *)a : nullptr);
     } else {
         constexpr int L = 128, NT = 512;
         constexpr size_t sm = lu_leaf_smem<float, L>();
@@ -256,7 +266,7 @@ cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int6
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         lu_leaf_kernel<float, L, NT><<<1, NT, sm, g.c->stream>>>((const float *)a, lda, (float *)ks, ldk, off,
-                                                                 nb, g.c->info);
+                                                                 nb, g.c->info, g.keep ? (float *)a : nullptr);
     }
     return cudaGetLastError();
 }
@@ -285,6 +295,13 @@ cudaError_t rec(const GenCtx &g, uint8_t *a, int64_t lda, uint8_t *ks, int64_t l
     e = product(g, GemmArgs{m2, m2, m1, -1.0, T2, m2, OP_FULL, T1, m1, OP_FULL, 1.0, A(m1, m1), lda, OP_FULL},
                 "gen:schur");
     if (e != cudaSuccess) return e;
+    if (g.keep) {   // A12 <- U12, A21 <- L21 (the originals are no longer needed)
+        e = cudaMemcpy2DAsync(A(0, m1), lda * es, T1, m1 * es, m1 * es, m2, cudaMemcpyDeviceToDevice, g.c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(A(m1, 0), lda * es, T2, m2 * es, m2 * es, m1, cudaMemcpyDeviceToDevice,
+                                  g.c->stream);
+        if (e != cudaSuccess) return e;
+    }
     e = rec(g, a, lda, ks, ldk, off + m1, m2, depth + 1);
     if (e != cudaSuccess) return e;
     // K21 = -K22 (L21 K11)
@@ -300,6 +317,30 @@ cudaError_t rec(const GenCtx &g, uint8_t *a, int64_t lda, uint8_t *ks, int64_t l
     if (e != cudaSuccess) return e;
     return product(g, GemmArgs{m1, m2, m2, -1.0, T3, m1, OP_FULL, KS(m1, m1), ldk, OP_UPPER, 0.0, KS(0, m1), ldk,
                                OP_FULL}, "gen:s12b");
+}
+
+template <typename T>
+__global__ void take_diag_kernel(const T *__restrict__ a, int64_t lda, T *__restrict__ d, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = a[i + i * lda];
+}
+
+// Doolittle -> Crout with D = diag(U_d):  L = L_d D,  U = D^-1 U_d,  K = L^-1 = D^-1 K_d,
+// S = U^-1 = S_d D.  The diagonals stay: L_ii = d_i in a, and K_ii = 1/d_i = (S_d)_ii in sk.
+template <typename T>
+__global__ void crout_form_kernel(T *__restrict__ a, int64_t lda, T *__restrict__ sk, int64_t ldsk,
+                                  const T *__restrict__ d, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = blockIdx.y;
+    if (i >= n || i == j) return;
+    T *pa = a + i + j * lda, *ps = sk + i + j * ldsk;
+    if (i > j) {
+        *pa = *pa * d[j];
+        *ps = *ps / d[i];
+    } else {
+        *pa = *pa / d[i];
+        *ps = *ps * d[j];
+    }
 }
 
 }  // namespace
@@ -319,6 +360,33 @@ tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t l
     e = product(g, GemmArgs{n, n, n, 1.0, ks, ldk, OP_UPPER, ks, ldk, OP_LOWER_UNIT, 0.0, a, lda, OP_FULL},
                 "gen:sk");
     return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+size_t skul_ws_bytes(int64_t n, tri_dtype dt) {
+    if (n <= 0) return 0;
+    return gen_layout(n, dt, false).total + al((size_t)n * esz(dt));
+}
+
+// SKUL (Algorithm SKUL, Section 5.1): the recursion above with the factors kept, then the
+// Crout scaling, so that a = L\U (U unit upper) and sk = K\S (S unit upper).
+tri_status run_skul(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, void *ws) {
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;   // one grid row per column in crout_form_kernel
+    GenCtx g{&c, dt, (uint8_t *)ws, gen_layout(n, dt, false), leaf_size(dt), true};
+    cudaError_t e = rec(g, (uint8_t *)a, lda, (uint8_t *)sk, ldsk, 0, n, 0);
+    if (e != cudaSuccess) return TRI_ERR_CUDA;
+    void *d = g.ws + g.lay.total;
+    const unsigned rb = (unsigned)((n + 255) / 256);
+    TraceScope ts(c.stream, "skul:crout_form", 0.0, 6.0 * (double)n * n * esz(dt));
+    if (dt == TRI_F64) {
+        take_diag_kernel<double><<<rb, 256, 0, c.stream>>>((const double *)a, lda, (double *)d, n);
+        crout_form_kernel<double><<<dim3(rb, (unsigned)n), 256, 0, c.stream>>>((double *)a, lda, (double *)sk, ldsk,
+                                                                             (const double *)d, n);
+    } else {
+        take_diag_kernel<float><<<rb, 256, 0, c.stream>>>((const float *)a, lda, (float *)d, n);
+        crout_form_kernel<float><<<dim3(rb, (unsigned)n), 256, 0, c.stream>>>((float *)a, lda, (float *)sk, ldsk,
+                                                                            (const float *)d, n);
+    }
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 
 }  // namespace triinv

@@ -65,6 +65,13 @@ def _declare(lib):
         "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
         "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
+        "skul": ([i64, vp, i64, vp, i64, i32, vp], i32),
+        "skul_workspace_size": ([i64, i32], sz),
+        "skul_ex": ([i64, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+        "sqr": ([i64, vp, i64, vp, i64, vp, i64, i32, vp], i32),
+        "sqr_workspace_size": ([i64, i32], sz),
+        "sqr_ex": ([i64, vp, i64, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+        "sqr_inv": ([i64, vp, i64, i32, vp], i32),
         "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
                               vp, i64, vp], i32),
         "tri_mixed_schedule_stats": ([i64, i32, ctypes.POINTER(ctypes.c_double), i32], i32),
@@ -129,6 +136,35 @@ def gen_inv_workspace_size(n, dtype) -> int:
 
 def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
     return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, stream or None)
+
+
+def skul(n, a_ptr, lda, sk_ptr, ldsk, dtype, stream=0) -> int:
+    return load().skul(n, a_ptr, lda, sk_ptr, ldsk, dtype, stream or None)
+
+
+def skul_workspace_size(n, dtype) -> int:
+    return int(load().skul_workspace_size(n, dtype))
+
+
+def skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace, ws_bytes, stream=0) -> int:
+    return load().skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace or None, ws_bytes, stream or None)
+
+
+def sqr(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, stream=0) -> int:
+    return load().sqr(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, stream or None)
+
+
+def sqr_workspace_size(n, dtype) -> int:
+    return int(load().sqr_workspace_size(n, dtype))
+
+
+def sqr_ex(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, workspace, ws_bytes, stream=0) -> int:
+    return load().sqr_ex(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, workspace or None, ws_bytes,
+                         stream or None)
+
+
+def sqr_inv(n, a_ptr, lda, dtype, stream=0) -> int:
+    return load().sqr_inv(n, a_ptr, lda, dtype, stream or None)
 
 
 def _arrays(sizes, ptrs):
@@ -398,6 +434,50 @@ def general_inv(a, mixed: bool = False, stream=None):
     n = out.shape[0]
     st = gen_inv(n, out.data_ptr(), max(1, out.stride(0)), _dtype_code(out, mixed), _stream_handle(stream))
     check(st, "gen_inv")
+    return out
+
+
+def skul_factors(a, mixed: bool = False, stream=None):
+    """SKUL (Algorithm SKUL, Section 5.1) of a square CUDA tensor: returns (L, U, S, K)
+    with A = L U (L lower, U unit upper, Crout), S = U^-1, K = L^-1 and A^-1 = S K.  The
+    C call works on the column-major layout of A, i.e. the row-major buffer of A^T."""
+    import torch
+    _rowmajor_square(a)
+    buf = a.t().contiguous()          # column-major A
+    sk = torch.empty_like(buf)
+    n = buf.shape[0]
+    ld = max(1, n)
+    st = skul(n, buf.data_ptr(), ld, sk.data_ptr(), ld, _dtype_code(buf, mixed), _stream_handle(stream))
+    check(st, "skul")
+    lu, ks = buf.t(), sk.t()          # back to the logical matrices
+    eye = torch.eye(n, dtype=a.dtype, device=a.device)
+    return torch.tril(lu), torch.triu(lu, 1) + eye, torch.triu(ks, 1) + eye, torch.tril(ks)
+
+
+def sqr_factors(a, mixed: bool = False, stream=None):
+    """SQR (Algorithm SQR, Section 5.1) of a square CUDA tensor: returns (Q, R, S) with
+    A = Q R (R upper, positive diagonal) and S = R^-1, so A^-1 = S Q^T."""
+    import torch
+    _rowmajor_square(a)
+    q = a.t().contiguous()            # column-major A
+    r = torch.empty_like(q)
+    s = torch.empty_like(q)
+    n = q.shape[0]
+    ld = max(1, n)
+    st = sqr(n, q.data_ptr(), ld, r.data_ptr(), ld, s.data_ptr(), ld, _dtype_code(q, mixed),
+             _stream_handle(stream))
+    check(st, "sqr")
+    return q.t(), r.t(), s.t()
+
+
+def qr_inv(a, mixed: bool = False, stream=None):
+    """Out of place A^-1 = S Q^T through SQR (no pivoting needed).  Row-major A is the
+    column-major A^T, whose inverse is (A^-1)^T: the row-major result is A^-1."""
+    _rowmajor_square(a)
+    out = a.contiguous().clone()
+    n = out.shape[0]
+    st = sqr_inv(n, out.data_ptr(), max(1, out.stride(0)), _dtype_code(out, mixed), _stream_handle(stream))
+    check(st, "sqr_inv")
     return out
 
 

@@ -147,3 +147,44 @@ def test_combrit_argument_errors_need_no_gpu(libtri):
     assert lib.tri_inv_combrit(0, 0, 0, 0, 1, lib.TRI_F64, 8) == lib.TRI_OK       # n == 0: no-op
     assert lib.tri_inv_combrit(0, 0, 16, 0, 16, lib.TRI_F32, 2) == A             # NULL
     assert lib.tri_inv_combrit(0, 0, 16, 4096, 15, lib.TRI_F32, 2) == A          # lda < n
+
+
+def test_skul_argument_errors_need_no_gpu(libtri):
+    A = lib.TRI_ERR_ARG
+    assert lib.skul(-1, 4096, 1, 8192, 1, lib.TRI_F32) == A
+    assert lib.skul(0, 0, 1, 0, 1, lib.TRI_F32) == lib.TRI_OK                # n == 0: no-op
+    assert lib.skul(8, 0, 8, 8192, 8, lib.TRI_F32) == A                      # NULL a
+    assert lib.skul(8, 4096, 8, 0, 8, lib.TRI_F32) == A                      # NULL sk
+    assert lib.skul(8, 4096, 8, 4096, 8, lib.TRI_F32) == A                   # a == sk
+    assert lib.skul(8, 4096, 7, 8192, 8, lib.TRI_F32) == A                   # lda < n
+    assert lib.skul(8, 4096, 8, 8192, 7, lib.TRI_F64) == A                   # ldsk < n
+    assert lib.skul(8, 4096, 8, 8192, 8, 9) == A                             # dtype
+    assert lib.skul(70000, 4096, 70000, 8192, 70000, lib.TRI_F32) == lib.TRI_ERR_UNSUPPORTED
+    need = lib.skul_workspace_size(1000, lib.TRI_F32)
+    assert need > 0 and lib.skul_workspace_size(0, lib.TRI_F32) == 0
+    # the K\S buffer is the caller's: less scratch than gen_inv by about n^2 elements
+    assert need < lib.gen_inv_workspace_size(1000, lib.TRI_F32)
+    assert lib.skul_ex(1000, 4096, 1000, 8192, 1000, lib.TRI_F32, 256, need - 1) == lib.TRI_ERR_NOMEM
+    assert lib.skul_ex(1000, 4096, 1000, 8192, 1000, lib.TRI_F32, 264, need) == lib.TRI_ERR_NOMEM
+
+
+def test_sqr_argument_errors_need_no_gpu(libtri):
+    A = lib.TRI_ERR_ARG
+    n = 8
+    assert lib.sqr(-1, 4096, 1, 8192, 1, 16384, 1, lib.TRI_F32) == A
+    assert lib.sqr(0, 0, 1, 0, 1, 0, 1, lib.TRI_F32) == lib.TRI_OK                 # n == 0: no-op
+    assert lib.sqr(n, 0, n, 8192, n, 16384, n, lib.TRI_F32) == A                   # NULL a
+    assert lib.sqr(n, 4096, n, 8192, n, 0, n, lib.TRI_F32) == A                    # NULL s
+    assert lib.sqr(n, 4096, n - 1, 8192, n, 16384, n, lib.TRI_F32) == A            # lda < n
+    assert lib.sqr(n, 4096, n, 8192, n, 16384, n, 9) == A                          # dtype
+    # overlapping outputs (r starts inside a's n x n footprint)
+    assert lib.sqr_ex(n, 4096, n, 4096 + 64, n, 16384, n, lib.TRI_F32, 256, 1 << 20) == A
+    assert lib.sqr_ex(n, 4096, n, 8192, n, 8192, n, lib.TRI_F64, 256, 1 << 20) == A  # r == s
+    assert lib.sqr(70000, 4096, 70000, 8192, 70000, 16384, 70000, lib.TRI_F32) == lib.TRI_ERR_UNSUPPORTED
+    need = lib.sqr_workspace_size(1000, lib.TRI_F32)
+    assert need > 0 and lib.sqr_workspace_size(0, lib.TRI_F32) == 0
+    assert lib.sqr_ex(1000, 4096, 1000, 1 << 24, 1000, 1 << 25, 1000, lib.TRI_F32, 256, need - 1) \
+        == lib.TRI_ERR_NOMEM
+    assert lib.sqr_inv(-1, 4096, 1, lib.TRI_F32) == A
+    assert lib.sqr_inv(0, 0, 1, lib.TRI_F32) == lib.TRI_OK
+    assert lib.sqr_inv(4, 0, 4, lib.TRI_F32) == A
