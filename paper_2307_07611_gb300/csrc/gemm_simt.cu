@@ -279,15 +279,17 @@ cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char 
         return cudaErrorInvalidValue;
     TraceScope ts(c.stream, trace_name, gemm_flops(g) * (double)(g.batch * g.batch2), 0.0);
     if (dt == TRI_F64) return launch_f64(c, g);
-    if (g.m >= 128 && g.n >= 128) return launch_g<float, 128, 128, 8, 8, 8>(c, g);
+    const bool big = g.m >= 128 && g.n >= 128;
+    const int64_t bt = big ? 128 : 64;
     int ksplit = 1;
     const int64_t mats = g.batch * g.batch2;
-    const int64_t tiles = ((g.m + 63) / 64) * ((g.n + 63) / 64) * mats;
+    const int64_t tiles = ((g.m + bt - 1) / bt) * ((g.n + bt - 1) / bt) * mats;
     if (g.split_k && g.beta == 0.0 && tiles < 2 * (int64_t)c.sm_count) {
         const int64_t want = (2 * (int64_t)c.sm_count + tiles - 1) / tiles;
-        const int64_t most = std::max<int64_t>(1, g.k / 64);   // at least 64 of k per slice
+        const int64_t most = std::max<int64_t>(1, g.k / 128);   // at least 128 of k per slice
         ksplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 64, 65535 / mats}));
     }
+    if (big) return launch_g<float, 128, 128, 8, 8, 8>(c, g, ksplit);
     return launch_g<float, 64, 64, 16, 4, 4>(c, g, ksplit);
 }
 

@@ -31,79 +31,125 @@ namespace {
 
 constexpr int kPanelThreads = 256;
 constexpr int kChunk = 64;          // rows of the panel staged in shared memory at a time
-constexpr int kMaxPanelCtas = 64;   // partial Gram matrices reduced by the Cholesky kernel
+constexpr int kMaxPanelCtas = 128;
+
+// 16-byte shared-memory vector load / store of 16 / sizeof(T) elements.
+template <typename T>
+__device__ __forceinline__ void ld16(T (&v)[16 / sizeof(T)], const T *p) {
+    *reinterpret_cast<uint4 *>(v) = *reinterpret_cast<const uint4 *>(p);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T *p, const T (&v)[16 / sizeof(T)]) {
+    *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(v);
+}
 
 // One pass over the rows of a leaf panel P (rows x m, m <= W), CTA b taking rows
-// [b * rows_per, (b + 1) * rows_per):
-//   sapply != null:   P <- P S  (S upper, W x W, leading dimension W)
-//   partials != null: the CTA's partial Gram matrix of the (updated) rows, W x W, into
-//                     partials + b * W * W
+// [b * rows_per, (b + 1) * rows_per) in chunks of kChunk rows, staged transposed
+// (s_pt[c][r] = P(r0 + r, c), a column per shared-memory row):
+//   sapply != null: P <- P S  (S upper, W x W, leading dimension W)
+//   gram != null:   G += P^T P of the (updated) rows, upper triangle, atomically
+//                   (G is W x W, zero on entry to the first pass of a leaf)
 template <typename T, int W>
 __global__ void __launch_bounds__(kPanelThreads) qr_panel_kernel(T *p, int64_t ldp, int64_t rows, int m,
-                                                                 const T *__restrict__ sapply,
-                                                                 T *__restrict__ partials, int64_t rows_per) {
+                                                                 const T *__restrict__ sapply, T *gram,
+                                                                 int64_t rows_per) {
     constexpr int NT = kPanelThreads, CH = kChunk;
-    constexpr int AJ = NT / CH;          // column groups of the apply step
-    constexpr int AQ = W / AJ;           // outputs per thread per chunk (apply)
-    constexpr int GJ = NT / W;           // column groups of the Gram step
-    constexpr int GQ = W / GJ;           // Gram entries per thread
-    __shared__ T s_s[W][W + 1];
-    __shared__ T s_p[CH][W + 1];
+    constexpr int V = 16 / sizeof(T);    // elements per 16-byte vector
+    constexpr int PT = CH + V;           // row pitch: an odd number of 16-byte vectors
+    constexpr int PS = W + V;
+    constexpr int CB = W / 16;           // columns per thread
+    constexpr int RB = CH / 16;          // rows per thread (apply)
+    static_assert((PT / V) % 2 == 1 && CB % V == 0 && RB % V == 0, "panel layout");
+    __shared__ __align__(16) T s_s[W][PS];
+    __shared__ __align__(16) T s_pt[W][PT];
     const int tid = threadIdx.x;
-    if (sapply)
-        for (int idx = tid; idx < W * W; idx += NT) {
-            const int i = idx % W, j = idx / W;
-            s_s[i][j] = (i <= j && j < m) ? sapply[i + j * W] : T(0);
-        }
-    T g[GQ];
+    static_assert((W * W) % NT == 0 && (CH * W) % NT == 0, "panel loops");
+    if (sapply) {
 #pragma unroll
-    for (int q = 0; q < GQ; ++q) g[q] = T(0);
-    const int gi = tid % W, gj = tid / W;
-    const int ar = tid % CH, aj = tid / CH;
+        for (int it = 0; it < W * W / NT; ++it) {
+            const int idx = tid + it * NT, k = idx % W, j = idx / W;
+            s_s[k][j] = (k <= j && j < m) ? sapply[k + j * W] : T(0);
+        }
+    }
+    const int ti = tid % 16, tj = tid / 16;   // Gram entries (ti + 16 ii, tj + 16 jj)
+    const int tr = tid % 16, tc = tid / 16;   // apply outputs rows tr*RB.., columns tc*CB..
+    T g[CB][CB];
+#pragma unroll
+    for (int a = 0; a < CB; ++a)
+#pragma unroll
+        for (int b = 0; b < CB; ++b) g[a][b] = T(0);
     const int64_t r_begin = (int64_t)blockIdx.x * rows_per;
     const int64_t r_end = min(rows, r_begin + rows_per);
     for (int64_t r0 = r_begin; r0 < r_end; r0 += CH) {
-        for (int idx = tid; idx < CH * W; idx += NT) {
-            const int r = idx % CH, c = idx / CH;
+#pragma unroll
+        for (int it = 0; it < CH * W / NT; ++it) {
+            const int idx = tid + it * NT, r = idx % CH, c = idx / CH;
             const int64_t gr = r0 + r;
-            s_p[r][c] = (gr < r_end && c < m) ? p[gr + (int64_t)c * ldp] : T(0);
+            s_pt[c][r] = (gr < r_end && c < m) ? p[gr + (int64_t)c * ldp] : T(0);
         }
         __syncthreads();
         if (sapply) {
-            T acc[AQ];
+            T acc[RB][CB];
 #pragma unroll
-            for (int q = 0; q < AQ; ++q) acc[q] = T(0);
-#pragma unroll 8
-            for (int k = 0; k < W; ++k) {
-                const T v = s_p[ar][k];
+            for (int a = 0; a < RB; ++a)
 #pragma unroll
-                for (int q = 0; q < AQ; ++q) acc[q] = fma(v, s_s[k][aj + AJ * q], acc[q]);
-            }
-            __syncthreads();
-            const int64_t gr = r0 + ar;
-#pragma unroll
-            for (int q = 0; q < AQ; ++q) {
-                const int j = aj + AJ * q;
-                s_p[ar][j] = acc[q];
-                if (gr < r_end && j < m) p[gr + (int64_t)j * ldp] = acc[q];
-            }
-            __syncthreads();
-        }
-        if (partials) {
+                for (int b = 0; b < CB; ++b) acc[a][b] = T(0);
 #pragma unroll 4
-            for (int r = 0; r < CH; ++r) {
-                const T v = s_p[r][gi];
+            for (int k = 0; k < W; ++k) {
+                T av[RB], bv[CB];
 #pragma unroll
-                for (int q = 0; q < GQ; ++q) g[q] = fma(v, s_p[r][gj + GJ * q], g[q]);
+                for (int u = 0; u < RB / V; ++u) ld16<T>(*reinterpret_cast<T (*)[V]>(av + u * V), &s_pt[k][tr * RB + u * V]);
+#pragma unroll
+                for (int u = 0; u < CB / V; ++u) ld16<T>(*reinterpret_cast<T (*)[V]>(bv + u * V), &s_s[k][tc * CB + u * V]);
+#pragma unroll
+                for (int a = 0; a < RB; ++a)
+#pragma unroll
+                    for (int b = 0; b < CB; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < CB; ++b)
+#pragma unroll
+                for (int u = 0; u < RB / V; ++u) {
+                    T w[V];
+#pragma unroll
+                    for (int x = 0; x < V; ++x) w[x] = acc[u * V + x][b];
+                    st16<T>(&s_pt[tc * CB + b][tr * RB + u * V], w);
+                }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < CH * W / NT; ++it) {
+                const int idx = tid + it * NT, r = idx % CH, c = idx / CH;
+                const int64_t gr = r0 + r;
+                if (gr < r_end && c < m) p[gr + (int64_t)c * ldp] = s_pt[c][r];
+            }
+        }
+        if (gram) {
+#pragma unroll 2
+            for (int r = 0; r < CH; r += V) {
+                T av[CB][V], bv[CB][V];
+#pragma unroll
+                for (int a = 0; a < CB; ++a) ld16<T>(av[a], &s_pt[ti + 16 * a][r]);
+#pragma unroll
+                for (int b = 0; b < CB; ++b) ld16<T>(bv[b], &s_pt[tj + 16 * b][r]);
+#pragma unroll
+                for (int a = 0; a < CB; ++a)
+#pragma unroll
+                    for (int b = 0; b < CB; ++b)
+#pragma unroll
+                        for (int x = 0; x < V; ++x) g[a][b] = fma(av[a][x], bv[b][x], g[a][b]);
             }
         }
         __syncthreads();
     }
-    if (partials) {
-        T *out = partials + (size_t)blockIdx.x * W * W;
+    if (gram)
 #pragma unroll
-        for (int q = 0; q < GQ; ++q) out[gi + (gj + GJ * q) * W] = g[q];
-    }
+        for (int a = 0; a < CB; ++a)
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int i = ti + 16 * a, j = tj + 16 * b;
+                if (i <= j && j < m) atomicAdd(gram + i + j * W, g[a][b]);
+            }
 }
 
 template <typename T, int W>
@@ -115,15 +161,14 @@ constexpr size_t chol_smem() {
 }
 
 // The Cholesky step of one Cholesky QR pass, one CTA:
-//   G = sum of the partial Gram matrices (m x m, identity beyond m),
+//   G = the accumulated Gram matrix (m x m, identity beyond m; its buffer is cleared),
 //   G = R^T R (R upper, positive diagonal), S = R^-1.
 // pass 0: S -> sapply, R -> keep.
 // pass 1: with S1 = sapply and R1 = keep from pass 0: S2 -> sapply, R2 R1 -> rblk and
 //         S1 S2 -> sblk (their m x m upper triangles).
 template <typename T, int W>
-__global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(const T *__restrict__ partials, int np, int m,
-                                                                int pass, T *sapply, T *keep, T *rblk,
-                                                                int64_t ldr, T *sblk, int64_t lds,
+__global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(T *gram, int m, int pass, T *sapply, T *keep,
+                                                                T *rblk, int64_t ldr, T *sblk, int64_t lds,
                                                                 long long *info, int64_t col0) {
     constexpr int NT = kPanelThreads;
     constexpr int EQ = W * W / NT;       // entries per thread
@@ -138,36 +183,44 @@ __global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(const T *__restr
     T *wt = tiles + (size_t)(nt * (nt + 1) / 2) * TE;
     const int tid = threadIdx.x;
 
-    // entries e = tid + NT q:  i = e % W, j = e / W
+    // entries e = tid + NT q:  i = e % W, j = e / W; the Gram matrix is read and its
+    // buffer cleared for the next pass
     T v[EQ];
 #pragma unroll
     for (int q = 0; q < EQ; ++q) {
         const int e = tid + NT * q, i = e % W, j = e / W;
-        T acc = T(0);
-        if (i <= j && j < m)
-            for (int b = 0; b < np; ++b) acc += partials[(size_t)b * W * W + e];
-        else if (i == j)
-            acc = T(1);
-        v[q] = acc;
+        T val = T(0);
+        if (i <= j && j < m) {
+            val = gram[e];
+            gram[e] = T(0);
+        } else if (i == j) {
+            val = T(1);
+        }
+        v[q] = val;
     }
     // Cholesky, right-looking, one barrier per step: the owners of row k publish it,
     // every thread then scales (row k) or updates (rows below) its own entries.
+    const int i0 = tid % W, j0 = tid / W;     // entries (i0, j0 + (NT / W) q)
     for (int k = 0; k < m; ++k) {
         T *rk = rowk + (k & 1) * W;
+        if (i0 == k) {
 #pragma unroll
-        for (int q = 0; q < EQ; ++q) {
-            const int e = tid + NT * q, i = e % W, j = e / W;
-            if (i == k && j >= k) rk[j] = v[q];
+            for (int q = 0; q < EQ; ++q) {
+                const int j = j0 + (NT / W) * q;
+                if (j >= k) rk[j] = v[q];
+            }
         }
         __syncthreads();
         const T d = rk[k];
         if (tid == 0 && !(d > T(0) && isfinite(d))) atomicMin(info, (long long)(col0 + k));
-        const T piv = sqrt(d), rd = T(1) / d;
+        const T rp = T(1) / sqrt(d);          // R_kj = G_kj / sqrt(d)
+        const T li = rk[i0] * rp;             // R_k,i0 (this thread's row i0)
 #pragma unroll
         for (int q = 0; q < EQ; ++q) {
-            const int e = tid + NT * q, i = e % W, j = e / W;
-            if (i == k && j >= k) v[q] = v[q] / piv;
-            else if (i > k && j >= i) v[q] = fma(-rk[i] * rd, rk[j], v[q]);
+            const int j = j0 + (NT / W) * q;
+            const T rkj = rk[j] * rp;
+            if (i0 == k && j >= k) v[q] = rkj;
+            else if (i0 > k && j >= i0) v[q] = fma(-li, rkj, v[q]);
         }
     }
 #pragma unroll
@@ -207,18 +260,43 @@ __global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(const T *__restr
         x2[i][j] = sapply[idx];
     }
     __syncthreads();
-    for (int idx = tid; idx < W * W; idx += NT) {
-        const int i = idx % W, j = idx / W;
-        sapply[idx] = sm[i][j];
-        if (i > j || j >= m) continue;
-        T r = T(0), s = T(0);
-        for (int k = i; k <= j; ++k) {
-            r = fma(g[i][k], x1[k][j], r);    // (R2 R1)_ij
-            s = fma(x2[i][k], sm[k][j], s);   // (S1 S2)_ij
+    // (R2 R1)_ij and (S1 S2)_ij over all k: the triangles' stored zeros drop the terms
+    // outside i <= k <= j, so every lane runs the same loop.
+    T racc[EQ], sacc[EQ];
+#pragma unroll
+    for (int q = 0; q < EQ; ++q) racc[q] = sacc[q] = T(0);
+#pragma unroll 4
+    for (int k = 0; k < W; ++k) {
+        const T a = g[i0][k], b = x2[i0][k];
+#pragma unroll
+        for (int q = 0; q < EQ; ++q) {
+            const int j = j0 + (NT / W) * q;
+            racc[q] = fma(a, x1[k][j], racc[q]);
+            sacc[q] = fma(b, sm[k][j], sacc[q]);
         }
-        rblk[i + j * ldr] = r;
-        sblk[i + j * lds] = s;
     }
+#pragma unroll
+    for (int q = 0; q < EQ; ++q) {
+        const int j = j0 + (NT / W) * q;
+        sapply[i0 + j * W] = sm[i0][j];
+        if (i0 <= j && j < m) {
+            rblk[i0 + j * ldr] = racc[q];
+            sblk[i0 + j * lds] = sacc[q];
+        }
+    }
+}
+
+// C = alpha * sum_b P_b (+ beta C): the slices of a split-k product, summed in order.
+__global__ void sum_slices_kernel(float *c, int64_t ldc, const float *__restrict__ parts, int64_t m, int64_t n,
+                                  int slices, float alpha, float beta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = blockIdx.y;
+    if (i >= m) return;
+    const float *pp = parts + i + j * m;
+    float acc = 0.f;
+    for (int b = 0; b < slices; ++b) acc += pp[(size_t)b * m * n];
+    float *pc = c + i + j * ldc;
+    *pc = beta == 0.f ? alpha * acc : fmaf(alpha, acc, beta * *pc);
 }
 
 template <typename T>
@@ -238,16 +316,21 @@ int64_t split_point(int64_t m, int w) {
 }
 
 struct QrLayout {
-    size_t partials, sapply, keep, tmp, planes, total;
+    size_t gram, sapply, keep, tmp, parts, planes, total;
 };
+
+// Split-k tensor-core products (mixed): slices s with s * tiles <= 2 * kMaxSm, so the
+// partial outputs hold at most 2 * kMaxSm tensor-core tiles of 128 x 256.
+constexpr int64_t kMaxSm = 160;
+constexpr size_t kPartsElems = (size_t)2 * kMaxSm * 128 * 256;
 
 QrLayout qr_layout(int64_t n, tri_dtype dt) {
     QrLayout l{};
     const size_t es = esz(dt);
     const int w = leaf_w(dt);
     size_t o = 0;
-    l.partials = o;
-    o += al((size_t)kMaxPanelCtas * w * w * es);
+    l.gram = o;
+    o += al((size_t)w * w * es);
     l.sapply = o;
     o += al((size_t)w * w * es);
     l.keep = o;
@@ -255,6 +338,8 @@ QrLayout qr_layout(int64_t n, tri_dtype dt) {
     l.tmp = o;
     const int64_t h = split_point(n, w);
     o += n > w ? al((size_t)h * (n - h) * es) : 0;
+    l.parts = o;
+    if (dt == TRI_F32_MIXED && n > w) o += al(kPartsElems * 4);
     l.planes = o;
     if (dt == TRI_F32_MIXED && n > w) o += al(gemm_tc_ws_bytes(n, n, n));
     l.total = o;
@@ -273,14 +358,43 @@ struct QrCtx {
     int64_t rows_per;
 };
 
-constexpr int64_t kTcMin = 512;
-
-// Tensor cores (mixed) for products that are large and give the grid enough tiles; the
-// rest on CUDA cores, with the long-k products split over CTAs.
+// Tensor cores (mixed) for the products with at least 128 rows and columns and k >= 128
+// that fill the grid: directly when they have enough 128 x 256 output tiles, else (long
+// k) as `s` k-slices run as one batched product into separate partial outputs, summed in
+// a fixed order afterwards.  The rest on CUDA cores, with long-k products split over CTAs.
 cudaError_t product(const QrCtx &q, GemmArgs g, const char *name) {
-    if (q.dt == TRI_F32_MIXED && g.m >= kTcMin && g.n >= kTcMin && g.k >= kTcMin &&
-        ((g.m + 127) / 128) * ((g.n + 255) / 256) >= q.c->sm_count / 2)
-        return gemm_tc(*q.c, g, 3, q.ws + q.lay.planes, name);
+    if (q.dt == TRI_F32_MIXED && g.m >= 128 && g.n >= 128 && g.k >= 128 && g.batch == 1) {
+        const int64_t tiles = ((g.m + 127) / 128) * ((g.n + 255) / 256);
+        const int64_t sm = std::min<int64_t>(q.c->sm_count, kMaxSm);
+        if (tiles >= sm / 2 && g.m * g.n * g.k >= (int64_t)1 << 27)
+            return gemm_tc(*q.c, g, 3, q.ws + q.lay.planes, name);
+        int64_t sl = 1;
+        while (sl * 2 * tiles <= 2 * sm && g.k % (sl * 2) == 0 && g.k / (sl * 2) >= 1024) sl *= 2;
+        if (sl > 1 && g.akind == OP_FULL && g.bkind == OP_FULL && g.cmask == OP_FULL &&
+            (size_t)(sl * g.m * g.n) <= kPartsElems) {
+            const int64_t ks = g.k / sl;
+            float *parts = (float *)(q.ws + q.lay.parts);
+            GemmArgs gb = g;
+            gb.k = ks;
+            gb.batch = sl;
+            gb.sa = g.ta ? ks : ks * g.lda;    // slice b of op(A) = columns [b ks, (b+1) ks) of op(A)
+            gb.sb = g.tb ? ks * g.ldb : ks;    // and rows [b ks, (b+1) ks) of op(B)
+            gb.alpha = 1.0;
+            gb.beta = 0.0;
+            gb.c = parts;
+            gb.ldc = g.m;
+            gb.sc = g.m * g.n;
+            cudaError_t e = gemm_tc(*q.c, gb, 3, q.ws + q.lay.planes, name);
+            if (e != cudaSuccess) return e;
+            if (g.n > 65535) return cudaErrorInvalidValue;
+            dim3 grid((unsigned)((g.m + 255) / 256), (unsigned)g.n);
+            sum_slices_kernel<<<grid, 256, 0, q.c->stream>>>((float *)g.c, g.ldc, parts, g.m, g.n, (int)sl,
+                                                             (float)g.alpha, (float)g.beta);
+            return cudaGetLastError();
+        }
+        if (g.m >= 512 && g.k <= 1024 && tiles >= sm / 2)   // tall, short-k products
+            return gemm_tc(*q.c, g, 3, q.ws + q.lay.planes, name);
+    }
     g.split_k = true;
     return gemm_simt(*q.c, q.dt == TRI_F64 ? TRI_F64 : TRI_F32, g, name);
 }
@@ -289,18 +403,18 @@ template <typename T, int W>
 cudaError_t leaf_t(const QrCtx &q, int64_t c0, int m) {
     const size_t es = sizeof(T);
     T *p = (T *)(q.a + (size_t)(c0 * q.lda) * es);
-    T *partials = (T *)(q.ws + q.lay.partials), *sapply = (T *)(q.ws + q.lay.sapply), *keep = (T *)(q.ws + q.lay.keep);
+    T *gram = (T *)(q.ws + q.lay.gram), *sapply = (T *)(q.ws + q.lay.sapply), *keep = (T *)(q.ws + q.lay.keep);
     T *rblk = (T *)(q.r + (size_t)(c0 + c0 * q.ldr) * es), *sblk = (T *)(q.s + (size_t)(c0 + c0 * q.lds) * es);
     constexpr size_t sm = chol_smem<T, W>();
     cudaError_t e = cudaFuncSetAttribute(qr_chol_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const cudaStream_t st = q.c->stream;
     TraceScope ts(st, es == 8 ? "sqr_leaf_f64" : "sqr_leaf_f32", 8.0 * (double)q.n * m * m, 0.0);
-    qr_panel_kernel<T, W><<<q.np, kPanelThreads, 0, st>>>(p, q.lda, q.n, m, nullptr, partials, q.rows_per);
-    qr_chol_kernel<T, W><<<1, kPanelThreads, sm, st>>>(partials, q.np, m, 0, sapply, keep, rblk, q.ldr, sblk, q.lds,
+    qr_panel_kernel<T, W><<<q.np, kPanelThreads, 0, st>>>(p, q.lda, q.n, m, nullptr, gram, q.rows_per);
+    qr_chol_kernel<T, W><<<1, kPanelThreads, sm, st>>>(gram, m, 0, sapply, keep, rblk, q.ldr, sblk, q.lds,
                                                        q.c->info, c0);
-    qr_panel_kernel<T, W><<<q.np, kPanelThreads, 0, st>>>(p, q.lda, q.n, m, sapply, partials, q.rows_per);
-    qr_chol_kernel<T, W><<<1, kPanelThreads, sm, st>>>(partials, q.np, m, 1, sapply, keep, rblk, q.ldr, sblk, q.lds,
+    qr_panel_kernel<T, W><<<q.np, kPanelThreads, 0, st>>>(p, q.lda, q.n, m, sapply, gram, q.rows_per);
+    qr_chol_kernel<T, W><<<1, kPanelThreads, sm, st>>>(gram, m, 1, sapply, keep, rblk, q.ldr, sblk, q.lds,
                                                        q.c->info, c0);
     qr_panel_kernel<T, W><<<q.np, kPanelThreads, 0, st>>>(p, q.lda, q.n, m, sapply, nullptr, q.rows_per);
     return cudaGetLastError();
@@ -379,10 +493,11 @@ size_t sqr_ws_bytes(int64_t n, tri_dtype dt) {
 tri_status run_sqr(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s,
                    int64_t lds, void *ws) {
     const size_t es = esz(dt);
-    if (cudaMemset2DAsync(r, ldr * es, 0, n * es, n, c.stream) != cudaSuccess ||
-        cudaMemset2DAsync(s, lds * es, 0, n * es, n, c.stream) != cudaSuccess)
-        return TRI_ERR_CUDA;
     QrCtx q = make_ctx(c, dt, n, a, lda, r, ldr, s, lds, ws);
+    if (cudaMemset2DAsync(r, ldr * es, 0, n * es, n, c.stream) != cudaSuccess ||
+        cudaMemset2DAsync(s, lds * es, 0, n * es, n, c.stream) != cudaSuccess ||
+        cudaMemsetAsync(q.ws + q.lay.gram, 0, (size_t)leaf_w(dt) * leaf_w(dt) * es, c.stream) != cudaSuccess)
+        return TRI_ERR_CUDA;
     return rec(q, 0, n) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 

@@ -101,6 +101,21 @@ def test_sqr_parity(lib, dt, n):
     assert residual(a, s @ q.T) <= (1e-13 if dt == "f64" else 5e-6)
 
 
+@pytest.mark.parametrize("n", [2048, 2500])
+def test_sqr_mixed_split_k_parity(lib, n):
+    """Sizes at which the mixed path runs Q1^T A2 on the tensor cores as k slices (two
+    slices at the top split, including the ragged 2500 = 1280 + 1220 columns)."""
+    a = inputs.general(n, seed=n + 11, dtype=np.float32).astype(np.float64)
+    (q, r, s), st = run_sqr(lib, a, "mixed")
+    assert st == lib.TRI_OK and lib.tri_get_info()[0] == lib.TRI_OK
+    want = oracle.sqr(a)
+    for name, g, w in zip("QRS", (q, r, s), want):
+        err = np.abs(g - w).max() / np.abs(w).max()
+        assert err <= 8 * tol(n, "mixed"), (name, err)
+    assert np.abs(q.T @ q - np.eye(n)).max() <= orth_tol(n, "mixed")
+    assert residual(a, s @ q.T) <= 5e-6
+
+
 @pytest.mark.parametrize("dt", ["f64", "f32", "mixed"])
 def test_sqr_paper_example(lib, dt):
     from tests._golden import matrices
