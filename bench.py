@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--cpu-sample-stride", type=int, default=1)
     p.add_argument("--profile-config", default=None,
                    choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512",
-                            "combrit_beta", "factor_f32_n16384"],
+                            "combrit_beta", "factor_f32_n16384", "factor_f32_n2048"],
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
@@ -373,10 +373,10 @@ def _secondary_factor(torch, lib, dev, out, only):
     (A = Q R with S = R^-1)."""
     import numpy as np
     from paper_2307_07611_gb300 import inputs
-    if only is not None and only != "factor_f32_n16384":
+    if only is not None and only not in ("factor_f32_n16384", "factor_f32_n2048"):
         return out
     sh = int(torch.cuda.current_stream().cuda_stream)
-    n = 16384
+    n = 2048 if only == "factor_f32_n2048" else 16384   # the small case is for profiler captures
     a = inputs.general(n, seed=0, dtype=np.float32)
     pr = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
     wk = torch.empty_like(pr)
@@ -390,7 +390,7 @@ def _secondary_factor(torch, lib, dev, out, only):
                                                              sh)), 2 if name == "mixed" else 1, 1,
                         setup=lambda: wk.copy_(pr))
         # ||L U - A|| on a sample of columns: column c of L U is L[:, :c+1] U[:c+1, c]
-        cols = [0, 8191, 16383]
+        cols = [0, n // 2 - 1, n - 1]
         lu = wk.T
         errs = []
         for c in cols:
@@ -401,7 +401,7 @@ def _secondary_factor(torch, lib, dev, out, only):
         res[name] = {"ms": ms, "value": 4 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "lu_column_err_max": max(errs)}
         del ws
     res["unit"] = "TFLOP/s (4n^3/3 executed: LU plus both inverse factors)"
-    out["skul_f32_n16384"] = res
+    out[f"skul_f32_n{n}"] = res
     # SQR: A = Q R with S = R^-1 (value by the MGS count 2n^3 + n^3/3 for S; the block
     # Gram-Schmidt re-orthogonalisation executes 2n^3 more)
     rr = torch.empty_like(pr)
@@ -413,13 +413,13 @@ def _secondary_factor(torch, lib, dev, out, only):
         ms = event_time(torch, lambda: lib.check(lib.sqr_ex(n, wk.data_ptr(), n, rr.data_ptr(), n, sk.data_ptr(), n,
                                                             code, wp, need, sh)), 2 if name == "mixed" else 1, 1,
                         setup=lambda: wk.copy_(pr))
-        cols = [0, 8191, 16383]
+        cols = [0, n // 2 - 1, n - 1]
         q = wk[cols, :].double()                         # rows of the buffer = columns of Q
         orth = float((q @ q.T - torch.eye(len(cols), dtype=torch.float64, device=dev)).abs().max())
         res[name] = {"ms": ms, "value": 7 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "sampled_orthogonality": orth}
         del ws
     res["unit"] = "TFLOP/s (7n^3/3: MGS QR 2n^3 plus S n^3/3)"
-    out["sqr_f32_n16384"] = res
+    out[f"sqr_f32_n{n}"] = res
     del pr, wk, sk, rr
     torch.cuda.empty_cache()
     return out
