@@ -26,24 +26,45 @@
 namespace triinv {
 namespace {
 
-// One leaf block [off, off + nb) of A (nb <= L): unpivoted Doolittle LU in shared memory,
-// then K = L^-1 (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
-// The two triangular inverses run on the tiled in-shared-memory split (tile_inverse.cuh):
-// L (unit diagonal) and U^T are copied into 32 x 32 tiles and inverted there.
+// One leaf block [off, off + nb) of A (nb <= L): unpivoted Doolittle LU, then K = L^-1
+// (strict lower part of ks) and S = U^-1 (upper part of ks, with diagonal).
+//
+// LU: the block sits in registers, warp w owning the BR x BC sub-block (w % WR, w / WR) of
+// it and lane (lr, lc) = (lane % 4, lane / 4) RPL rows x CPL columns of that.  Step k:
+// the owners of row k publish u_kj (j > k), the owners of column k publish a_ik (i > k)
+// and the owner of the pivot publishes 1/u_kk (buffers double-buffered by the parity of
+// k; the pivots are checked after the loop); one barrier; then every warp whose sub-block
+// has rows below k and columns from k on
+// sets l_ik = a_ik / u_kk and a_ij -= l_ik u_kj, the multipliers masked to zero outside the
+// trailing block so that every entry takes the same FMA; finished sub-blocks skip the step.
+// Column k of L is final at step k and goes straight to shared memory.
+// The inverses: L (unit diagonal) and U^T are copied into two sets of 32 x 32 tiles and
+// inverted together by the tiled split of tile_inverse.cuh.
 // lu_out (may be null, else the same matrix as a): the packed Doolittle factors of the
 // block are written back over it (L strictly below the diagonal, U on and above it).
 template <typename T, int L, int NT>
 __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T *__restrict__ ks, int64_t ldk,
                                                      int64_t off, int nb, long long *info, T *lu_out) {
-    constexpr int NTL = L / 32;                         // tile rows
-    constexpr int KT = NTL * (NTL + 1) / 2;             // lower tiles
+    constexpr int NW = NT / 32;
+    constexpr int WC = 4, WR = NW / WC;          // grid of warp sub-blocks
+    constexpr int BR = L / WR, BC = L / WC;      // sub-block of a warp
+    constexpr int RPL = BR / 4, CPL = BC / 8;    // rows / columns of a lane
+    static_assert(WR * WC == NW && RPL * 4 == BR && CPL * 8 == BC, "LU register layout");
+    constexpr int NTL = L / 32;                  // tile rows
+    constexpr int KT = NTL * (NTL + 1) / 2;      // lower tiles
     constexpr int WT = (NTL / 2) * (NTL / 2) > 0 ? (NTL / 2) * (NTL / 2) : 1;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T (*s)[L + 1] = reinterpret_cast<T (*)[L + 1]>(smem_raw);
-    T *tiles = reinterpret_cast<T *>(smem_raw + sizeof(T) * L * (L + 1));
-    T *wt = tiles + (size_t)KT * TE;
+    T *tl_ = reinterpret_cast<T *>(smem_raw + sizeof(T) * L * (L + 1));
+    T *tu_ = tl_ + (size_t)KT * TE;
+    T *wl_ = tu_ + (size_t)KT * TE;
+    T *wu_ = wl_ + (size_t)WT * TE;
+    T *rkb = wu_ + (size_t)WT * TE;              // 2 x L: row k
+    T *ckb = rkb + 2 * L;                        // 2 x L: column k
+    T *rpb = ckb + 2 * L;                        // 2: 1 / u_kk
+    T *pv = rpb + 2;                             // L: the pivots u_kk
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = NT / 32;
+    constexpr int nwarps = NW;
     for (int idx = tid; idx < L * L; idx += NT) {
         const int i = idx % L, j = idx / L;
         T v = (i == j) ? T(1) : T(0);
@@ -51,116 +72,118 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T 
         s[i][j] = v;
     }
     __syncthreads();
-    // Doolittle LU, right-looking, on register blocks: thread t owns rows 8*(t % RG) + r
-    // (r < 8) and columns CW*(t / RG) + c (c < CW) of the block.  Step k broadcasts row k
-    // (u_kj) and the scaled column k (l_ik) through shared memory (double-buffered by the
-    // parity of k), then every thread updates its block: a_ij -= l_ik u_kj.
     {
-        constexpr int RG = L / 8;                       // row groups
-        constexpr int CW = L * L / (NT * 8);            // columns per thread
-        static_assert(RG * (NT / RG) == NT && CW * (NT / RG) == L, "LU register layout");
-        T *rowk = tiles;                                // 2 x L scratch (tiles are free here)
-        T *colk = tiles + 2 * L;
-        const int rg = tid % RG, cg = tid / RG;
-        T v[8][CW];
+        const int wr = warp % WR, wc = warp / WR, lr = lane % 4, lc = lane / 4;
+        const int i0 = wr * BR + lr * RPL, j0 = wc * BC + lc * CPL;
+        T v[RPL][CPL];
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < RPL; ++r)
 #pragma unroll
-            for (int c = 0; c < CW; ++c) v[r][c] = s[rg * 8 + r][cg * CW + c];
-        __syncthreads();
-        for (int k = 0; k < nb; ++k) {
-            T *rk = rowk + (k & 1) * L;
-            T *ck = colk + (k & 1) * L;
-            if (rg == (k >> 3)) {
-                const int kr = k & 7;
+            for (int c = 0; c < CPL; ++c) v[r][c] = s[i0 + r][j0 + c];
+        // k = kb + kr with the inner step unrolled, so that row kr of a lane's block and
+        // its column kr % CPL are compile-time register indices (kb is a multiple of RPL,
+        // which CPL divides).
+        static_assert(RPL % CPL == 0, "step unrolling");
+        for (int kb = 0; kb < nb; kb += RPL) {
 #pragma unroll
-                for (int c = 0; c < CW; ++c) {
-                    T val = v[0][c];
+            for (int kr = 0; kr < RPL; ++kr) {
+                const int k = kb + kr;
+                if (k >= nb) break;
+                T *rk = rkb + (k & 1) * L, *ck = ckb + (k & 1) * L;
+                const bool own_col = j0 == kb + (kr / CPL) * CPL;
+                if (i0 == kb) {            // this lane holds row k: u_kj (j >= k)
 #pragma unroll
-                    for (int r = 1; r < 8; ++r) val = (r == kr) ? v[r][c] : val;
-                    rk[cg * CW + c] = val;
+                    for (int c = 0; c < CPL; ++c) {
+                        const T val = v[kr][c];
+                        if (j0 + c > k) rk[j0 + c] = val;
+                        if (j0 + c == k) {
+                            pv[k] = val;
+                            rpb[k & 1] = T(1) / val;
+                        }
+                    }
+                }
+                if (own_col)               // this lane holds column k: a_ik (i > k)
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r)
+                        if (i0 + r > k) ck[i0 + r] = v[r][kr % CPL];
+                __syncthreads();
+                if ((wr + 1) * BR - 1 > k && (wc + 1) * BC - 1 >= k) {
+                    // multipliers masked to the trailing block: rows i > k, columns j > k
+                    const T rp = rpb[k & 1];
+                    T li[RPL], uj[CPL];
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        const T l = ck[i0 + r] * rp;
+                        li[r] = (i0 + r > k) ? l : T(0);
+                    }
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) uj[c] = (j0 + c > k) ? rk[j0 + c] : T(0);
+                    if (own_col)           // column k of L is final: straight to shared memory
+#pragma unroll
+                        for (int r = 0; r < RPL; ++r)
+                            if (i0 + r > k) s[i0 + r][k] = li[r];
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r)
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c) v[r][c] = fma(-li[r], uj[c], v[r][c]);
                 }
             }
-            __syncthreads();
-            const T piv = rk[k];
-            if (tid == 0 && (piv == T(0) || !isfinite(piv))) atomicMin(info, (long long)(off + k));
-            const T rp = T(1) / piv;
-            if (cg == k / CW) {
-                const int kc = k % CW;
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int i = rg * 8 + r;
-                    T val = v[r][0];
-#pragma unroll
-                    for (int c = 1; c < CW; ++c) val = (c == kc) ? v[r][c] : val;
-                    const T l = val * rp;
-                    if (i > k) ck[i] = l;
-#pragma unroll
-                    for (int c = 0; c < CW; ++c) v[r][c] = (c == kc && i > k) ? l : v[r][c];
-                }
-            }
-            __syncthreads();
-            T lr[8], uc[CW];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) lr[r] = ck[rg * 8 + r];
-#pragma unroll
-            for (int c = 0; c < CW; ++c) uc[c] = rk[cg * CW + c];
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int c = 0; c < CW; ++c) {
-                    const int i = rg * 8 + r, j = cg * CW + c;
-                    if (i > k && j > k) v[r][c] = fma(-lr[r], uc[c], v[r][c]);
-                }
         }
-        __syncthreads();
+        // U (on and above the diagonal) from the registers; L is already in place
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < RPL; ++r)
 #pragma unroll
-            for (int c = 0; c < CW; ++c) s[rg * 8 + r][cg * CW + c] = v[r][c];
+            for (int c = 0; c < CPL; ++c)
+                if (j0 + c >= i0 + r) s[i0 + r][j0 + c] = v[r][c];
         __syncthreads();
     }
+    for (int k = tid; k < nb; k += NT)
+        if (pv[k] == T(0) || !isfinite(pv[k])) atomicMin(info, (long long)(off + k));
     if (lu_out)
         for (int idx = tid; idx < nb * nb; idx += NT) {
             const int i = idx % nb, j = idx / nb;
             lu_out[(off + i) + (off + j) * lda] = s[i][j];
         }
     const int nt = (nb + 31) / 32;
-    for (int pass = 0; pass < 2; ++pass) {
-        // pass 0: lower view = L (unit diagonal); pass 1: lower view = U^T.
-        for (int tl = warp; tl < nt * (nt + 1) / 2; tl += nwarps) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-            const int J = tl - I * (I + 1) / 2;
-            T *tp = tile_ptr(tiles, I, J);
-            for (int c = 0; c < 32; ++c) {
-                const int i = I * 32 + lane, j = J * 32 + c;
-                T v;
-                if (i >= nb || j >= nb) v = (i == j) ? T(1) : T(0);
-                else if (j > i) v = T(0);
-                else if (j == i) v = pass == 0 ? T(1) : s[i][i];
-                else v = pass == 0 ? s[i][j] : s[j][i];
-                tp[lane * TP + c] = v;
+    const int ntiles = nt * (nt + 1) / 2;
+    // tiles of the lower view: set 0 = L (unit diagonal), set 1 = U^T
+    for (int x = warp; x < 2 * ntiles; x += nwarps) {
+        const int set = x / ntiles, tl = x % ntiles;
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+        const int J = tl - I * (I + 1) / 2;
+        T *tp = tile_ptr(set == 0 ? tl_ : tu_, I, J);
+        for (int c = 0; c < 32; ++c) {
+            const int i = I * 32 + lane, j = J * 32 + c;
+            T v;
+            if (i >= nb || j >= nb) v = (i == j) ? T(1) : T(0);
+            else if (j > i) v = T(0);
+            else if (j == i) v = set == 0 ? T(1) : s[i][i];
+            else v = set == 0 ? s[i][j] : s[j][i];
+            tp[lane * TP + c] = v;
+        }
+    }
+    __syncthreads();
+    {
+        T *const tls[2] = {tl_, tu_};
+        T *const wts[2] = {wl_, wu_};
+        invert_tiles_multi<T, NT, 2>(tls, wts, nt, nb);
+    }
+    for (int x = warp; x < 2 * ntiles; x += nwarps) {
+        const int set = x / ntiles, tl = x % ntiles;
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+        const int J = tl - I * (I + 1) / 2;
+        const T *tp = tile_ptr(set == 0 ? tl_ : tu_, I, J);
+        for (int c = 0; c < 32; ++c) {
+            const int i = I * 32 + lane, j = J * 32 + c;
+            if (i >= nb || j >= nb || j > i) continue;
+            if (set == 0) {
+                if (j < i) ks[(off + i) + (off + j) * ldk] = tp[lane * TP + c];   // K, strict lower
+            } else {
+                ks[(off + j) + (off + i) * ldk] = tp[lane * TP + c];              // S = (U^T)^-1 ^T
             }
         }
-        __syncthreads();
-        invert_tiles<T, NT>(tiles, wt, nt, nb);
-        for (int tl = warp; tl < nt * (nt + 1) / 2; tl += nwarps) {
-            int I = 0;
-            while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-            const int J = tl - I * (I + 1) / 2;
-            const T *tp = tile_ptr(tiles, I, J);
-            for (int c = 0; c < 32; ++c) {
-                const int i = I * 32 + lane, j = J * 32 + c;
-                if (i >= nb || j >= nb || j > i) continue;
-                if (pass == 0) {
-                    if (j < i) ks[(off + i) + (off + j) * ldk] = tp[lane * TP + c];   // K, strict lower
-                } else {
-                    ks[(off + j) + (off + i) * ldk] = tp[lane * TP + c];              // S = (U^T)^-1 ^T
-                }
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -169,7 +192,7 @@ constexpr size_t lu_leaf_smem() {
     constexpr int NTL = L / 32;
     constexpr int KT = NTL * (NTL + 1) / 2;
     constexpr int WT = (NTL / 2) * (NTL / 2) > 0 ? (NTL / 2) * (NTL / 2) : 1;
-    return sizeof(T) * ((size_t)L * (L + 1) + (size_t)(KT + WT) * TE);
+    return sizeof(T) * ((size_t)L * (L + 1) + 2 * (size_t)(KT + WT) * TE + 5 * L + 2);
 }
 
 struct Node {

@@ -152,4 +152,79 @@ __device__ __forceinline__ int invert_tiles(T *tiles, T *wt, int nt, int n) {
     return r < (1 << 30) ? r : -1;
 }
 
+// invert_tiles for NM independent lower blocks at once (same order nt x nt tiles, same
+// valid order n): every stage's warp jobs of all blocks are spread over the NT / 32 warps,
+// so small blocks keep more warps busy.  tiles[x] / wt[x]: block x and its W scratch.
+// Pivot errors are not reported (the callers check their pivots before).  Ends with a
+// barrier.
+// p[x] without a dynamically indexed array (which would live in local memory).
+template <typename T, int NM>
+__device__ __forceinline__ T *pick(T *const (&p)[NM], int x) {
+    T *r = p[0];
+#pragma unroll
+    for (int i = 1; i < NM; ++i) r = (x == i) ? p[i] : r;
+    return r;
+}
+
+template <typename T, int NT, int NM>
+__device__ __forceinline__ void invert_tiles_multi(T *const (&tiles)[NM], T *const (&wt)[NM], int nt, int n) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+    for (int x = warp; x < NM * nt; x += nwarps) {
+        const int mtx = x / nt, I = x % nt;
+        warp_tile_inverse(tile_ptr(pick(tiles, mtx), I, I), lane, min(32, n - I * 32));
+    }
+    __syncthreads();
+    for (int ht = 1; ht < nt; ht *= 2) {
+        const int pairs = (nt - ht + 2 * ht - 1) / (2 * ht);
+        int jobs = 0;
+        for (int q = 0; q < pairs; ++q) jobs += min(ht, nt - (2 * q * ht + ht)) * ht;
+        for (int x = warp; x < NM * jobs; x += nwarps) {
+            const int mtx = x / jobs, jb = x % jobs;
+            T *tl = pick(tiles, mtx);
+            int q = 0, rest = jb;
+            for (;;) {
+                const int hc = min(ht, nt - (2 * q * ht + ht));
+                if (rest < hc * ht) break;
+                rest -= hc * ht;
+                ++q;
+            }
+            const int a0 = 2 * q * ht, c0 = a0 + ht;
+            const int Iw = rest / ht, Jw = rest % ht;
+            T acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+            for (int K = Jw; K < ht; ++K)
+                warp_mma32(tile_ptr(tl, c0 + Iw, a0 + K), tile_ptr(tl, a0 + K, a0 + Jw), acc, lane);
+            warp_store32(pick(wt, mtx) + (size_t)jb * TE, acc, lane, T(1));
+        }
+        __syncthreads();
+        for (int x = warp; x < NM * jobs; x += nwarps) {
+            const int mtx = x / jobs, jb = x % jobs;
+            T *tl = pick(tiles, mtx);
+            int q = 0, rest = jb, base = 0;
+            for (;;) {
+                const int hc = min(ht, nt - (2 * q * ht + ht));
+                if (rest < hc * ht) break;
+                rest -= hc * ht;
+                base += hc * ht;
+                ++q;
+            }
+            const int a0 = 2 * q * ht, c0 = a0 + ht;
+            const int Iw = rest / ht, Jw = rest % ht;
+            T acc[4][8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+            for (int K = 0; K <= Iw; ++K)
+                warp_mma32(tile_ptr(tl, c0 + Iw, c0 + K), pick(wt, mtx) + (size_t)(base + K * ht + Jw) * TE, acc, lane);
+            warp_store32(tile_ptr(tl, c0 + Iw, a0 + Jw), acc, lane, T(-1));
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace triinv
