@@ -84,6 +84,9 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T 
         // its column kr % CPL are compile-time register indices (kb is a multiple of RPL,
         // which CPL divides).
         static_assert(RPL % CPL == 0, "step unrolling");
+        // 1 / (this lane's candidate for the next pivot): computed at the end of the previous
+        // step's update, where it overlaps the remaining FMAs; only the pivot's owner stores it
+        T rcp_next = T(1) / v[0][0];
         for (int kb = 0; kb < nb; kb += RPL) {
 #pragma unroll
             for (int kr = 0; kr < RPL; ++kr) {
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T 
                         if (j0 + c > k) rk[j0 + c] = val;
                         if (j0 + c == k) {
                             pv[k] = val;
-                            rpb[k & 1] = T(1) / val;
+                            rpb[k & 1] = rcp_next;
                         }
                     }
                 }
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T 
                     for (int r = 0; r < RPL; ++r)
 #pragma unroll
                         for (int c = 0; c < CPL; ++c) v[r][c] = fma(-li[r], uj[c], v[r][c]);
+                    rcp_next = T(1) / v[(kr + 1) % RPL][(kr + 1) % CPL];
                 }
             }
         }
