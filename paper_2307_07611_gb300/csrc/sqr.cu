@@ -157,7 +157,7 @@ constexpr size_t chol_smem() {
     constexpr int nt = W / 32;
     constexpr int tiles = nt * (nt + 1) / 2;
     constexpr int wtiles = (nt / 2) * (nt / 2) > 0 ? (nt / 2) * (nt / 2) : 1;
-    return sizeof(T) * (4 * (size_t)W * (W + 1) + 2 * W + (size_t)(tiles + wtiles) * TE);
+    return sizeof(T) * (4 * (size_t)W * (W + 1) + 5 * W + 2 + (size_t)(tiles + wtiles) * TE);
 }
 
 // The Cholesky step of one Cholesky QR pass, one CTA:
@@ -178,55 +178,69 @@ __global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(T *gram, int m, 
     T (*sm)[W + 1] = g + W;                                          // S
     T (*x1)[W + 1] = g + 2 * W;                                      // R1 (pass 1)
     T (*x2)[W + 1] = g + 3 * W;                                      // S1 (pass 1)
-    T *rowk = reinterpret_cast<T *>(g + 4 * W);                      // 2 x W
-    T *tiles = rowk + 2 * W;
+    T *rowk = reinterpret_cast<T *>(g + 4 * W);                      // 2 x 2W: row k, padded
+    T *rsb = rowk + 4 * W;                                           // 2: 1 / sqrt(G_kk)
+    T *pvt = rsb + 2;                                                // W: the pivots G_kk
+    T *tiles = pvt + W;
     T *wt = tiles + (size_t)(nt * (nt + 1) / 2) * TE;
     const int tid = threadIdx.x;
 
-    // entries e = tid + NT q:  i = e % W, j = e / W; the Gram matrix is read and its
-    // buffer cleared for the next pass
+    // Cholesky, right-looking, one barrier per step.  Thread (ci, cg) = (tid % W, tid / W)
+    // holds the entries (ci, ci + cg + G q) of the upper triangle (G = NT / W; columns
+    // beyond W are padding), so its diagonal entry, when cg = 0, is always v[0].  Step k:
+    // the threads of row k publish it (unscaled) and its pivot's 1/sqrt, computed at the end
+    // of the previous step; one barrier; the rows below update, row k scales.  The Gram
+    // matrix is read and its buffer cleared for the next pass; pivots are checked after.
+    constexpr int G = NT / W;
+    const int ci = tid % W, cg = tid / W;
+    for (int x = tid; x < W * (W + 1); x += NT) (&g[0][0])[x] = T(0);
+    for (int x = tid; x < 4 * W; x += NT) rowk[x] = T(0);     // the padding columns stay zero
     T v[EQ];
 #pragma unroll
     for (int q = 0; q < EQ; ++q) {
-        const int e = tid + NT * q, i = e % W, j = e / W;
+        const int j = ci + cg + G * q;
         T val = T(0);
-        if (i <= j && j < m) {
-            val = gram[e];
-            gram[e] = T(0);
-        } else if (i == j) {
+        if (j < m) {
+            val = gram[ci + j * W];
+            gram[ci + j * W] = T(0);
+        } else if (j < W && j == ci) {
             val = T(1);
         }
         v[q] = val;
     }
-    // Cholesky, right-looking, one barrier per step: the owners of row k publish it,
-    // every thread then scales (row k) or updates (rows below) its own entries.
-    const int i0 = tid % W, j0 = tid / W;     // entries (i0, j0 + (NT / W) q)
+    T rs_next = T(1) / sqrt(v[0]);            // 1/sqrt(pivot) for the thread holding (0, 0)
+    __syncthreads();
     for (int k = 0; k < m; ++k) {
-        T *rk = rowk + (k & 1) * W;
-        if (i0 == k) {
+        T *rk = rowk + (k & 1) * 2 * W;
+        if (ci == k) {
 #pragma unroll
             for (int q = 0; q < EQ; ++q) {
-                const int j = j0 + (NT / W) * q;
-                if (j >= k) rk[j] = v[q];
+                const int j = ci + cg + G * q;
+                if (j < W) rk[j] = v[q];
+            }
+            if (cg == 0) {
+                pvt[k] = v[0];
+                rsb[k & 1] = rs_next;
             }
         }
         __syncthreads();
-        const T d = rk[k];
-        if (tid == 0 && !(d > T(0) && isfinite(d))) atomicMin(info, (long long)(col0 + k));
-        const T rp = T(1) / sqrt(d);          // R_kj = G_kj / sqrt(d)
-        const T li = rk[i0] * rp;             // R_k,i0 (this thread's row i0)
+        const T rs = rsb[k & 1];              // R_kj = G_kj / sqrt(G_kk)
+        if (ci > k) {
+            const T li = rk[ci] * rs;         // R_k,ci
 #pragma unroll
-        for (int q = 0; q < EQ; ++q) {
-            const int j = j0 + (NT / W) * q;
-            const T rkj = rk[j] * rp;
-            if (i0 == k && j >= k) v[q] = rkj;
-            else if (i0 > k && j >= i0) v[q] = fma(-li, rkj, v[q]);
+            for (int q = 0; q < EQ; ++q) v[q] = fma(-li, rk[ci + cg + G * q] * rs, v[q]);
+            if (cg == 0 && ci == k + 1) rs_next = T(1) / sqrt(v[0]);   // the next pivot's owner
+        } else if (ci == k) {
+#pragma unroll
+            for (int q = 0; q < EQ; ++q) v[q] *= rs;
         }
     }
+    if (tid < m && !(pvt[tid] > T(0) && isfinite(pvt[tid]))) atomicMin(info, (long long)(col0 + tid));
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < EQ; ++q) {
-        const int e = tid + NT * q, i = e % W, j = e / W;
-        g[i][j] = (i <= j) ? v[q] : T(0);
+        const int j = ci + cg + G * q;
+        if (j < W) g[ci][j] = v[q];
     }
     __syncthreads();
     // S = R^-1: invert the lower R^T in 32 x 32 tiles, S = ((R^T)^-1)^T.
@@ -261,7 +275,8 @@ __global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(T *gram, int m, 
     }
     __syncthreads();
     // (R2 R1)_ij and (S1 S2)_ij over all k: the triangles' stored zeros drop the terms
-    // outside i <= k <= j, so every lane runs the same loop.
+    // outside i <= k <= j, so every lane runs the same loop.  Entries (i0, j0 + G q).
+    const int i0 = tid % W, j0 = tid / W;
     T racc[EQ], sacc[EQ];
 #pragma unroll
     for (int q = 0; q < EQ; ++q) racc[q] = sacc[q] = T(0);
@@ -270,14 +285,14 @@ __global__ void __launch_bounds__(kPanelThreads) qr_chol_kernel(T *gram, int m, 
         const T a = g[i0][k], b = x2[i0][k];
 #pragma unroll
         for (int q = 0; q < EQ; ++q) {
-            const int j = j0 + (NT / W) * q;
+            const int j = j0 + G * q;
             racc[q] = fma(a, x1[k][j], racc[q]);
             sacc[q] = fma(b, sm[k][j], sacc[q]);
         }
     }
 #pragma unroll
     for (int q = 0; q < EQ; ++q) {
-        const int j = j0 + (NT / W) * q;
+        const int j = j0 + G * q;
         sapply[i0 + j * W] = sm[i0][j];
         if (i0 <= j && j < m) {
             rblk[i0 + j * ldr] = racc[q];
