@@ -217,6 +217,17 @@ TRI_API tri_status tri_batched_exec(tri_batched_plan *plan, void *stream);
 TRI_API tri_status tri_batched_plan_destroy(tri_batched_plan *plan);
 /* Thread count the autotuner chose for this plan (diagnostic). */
 TRI_API int tri_batched_plan_threads(const tri_batched_plan *plan);
+
+/* Growth limit of an FP32 plan: an FP64 leaf only for ill-conditioned blocks.  After a
+ * block's FP32 inverse, if max|X| * max|T| > tau (a lower bound of its condition number
+ * in the max norm) and the block has at most 128 rows, the block (still unchanged in
+ * memory) is inverted again in FP64 in shared memory and that result, rounded to FP32, is
+ * stored; larger blocks keep the FP32 result.  Default 1e4 for TRI_F32 and TRI_F32_MIXED
+ * plans (which run in FP32); tau <= 0 disables.  Synchronous; applies to later
+ * tri_batched_exec calls of the plan.
+ * Errors: TRI_ERR_ARG (null plan, NaN tau, another device current),
+ *         TRI_ERR_UNSUPPORTED (TRI_F64 plan). */
+TRI_API tri_status tri_batched_plan_set_growth_limit(tri_batched_plan *plan, double tau);
 TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs,
                                    tri_uplo uplo, tri_diag diag, tri_dtype dtype, void *stream);
 

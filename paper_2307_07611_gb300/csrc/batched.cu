@@ -22,6 +22,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -113,17 +114,23 @@ __device__ __forceinline__ void write_planes(const T *tiles, int nt, int n, long
 }
 
 // info_as >= 0: a zero pivot records info_as (the matrix of a batch) instead of the row.
-template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
+// S: the element type in global memory (T, or FP32 data inverted in FP64).
+// tau > 0 (FP32 only): growth limit.  When the FP32 inverse has max|X| * max|T| > tau and
+// the block has at most 128 rows, the block, still unchanged in global memory, is loaded
+// again and inverted in FP64 in the same shared memory, and that result is stored.
+template <typename T, bool TRANS, bool UNIT, int MAXT, int NT, typename S = T>
 __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
                                              long long ldp, long long ntot, __nv_bfloat16 *q0 = nullptr,
                                              __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr,
-                                             long long info_as = -1) {
+                                             long long info_as = -1, float tau = 0.f) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = NT / 32;
     const int n = d.n, nt = (n + 31) / 32;
-    const T *g = reinterpret_cast<const T *>(d.ptr);
+    const S *g = reinterpret_cast<const S *>(d.ptr);
     const long long ld = d.ld;
+    __shared__ unsigned s_tmax, s_xmax;      // max |T| and max |X| as float bits (tau > 0)
+    float tmax = 0.f;
 
     // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
     // One warp per tile.  FP32 tiles that lie inside the block, from a 16-byte aligned
@@ -131,7 +138,8 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     // consecutive elements along the contiguous index of the source); the rest as 32
     // scalar loads per lane.
     const int ntl = nt * (nt + 1) / 2;
-    const bool vec_ok = sizeof(T) == 4 && (((uintptr_t)g & 15) == 0) && (ld % 4 == 0);
+    const bool vec_ok = sizeof(S) == 4 && (((uintptr_t)g & 15) == 0) && (ld % 4 == 0);
+    if (tau > 0.f && tid == 0) s_tmax = s_xmax = 0u;
     for (int tl = warp; tl < ntl; tl += nwarps) {
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= tl) ++I;
@@ -157,6 +165,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
                     const int r = TRANS ? other : q4 + q, c = TRANS ? q4 + q : other;
                     T x = (T)vv[q];
                     if (I == J) x = c > r ? T(0) : (c == r && UNIT ? T(1) : x);
+                    tmax = fmaxf(tmax, fabsf((float)x));
                     tp[r * TP + c] = x;
                 }
             }
@@ -169,8 +178,8 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             const int r = TRANS ? q : lane, c = TRANS ? lane : q;
             const int gi = I * 32 + r, gj = J * 32 + c;
             if (gi < n && gj < n) {
-                if (gj < gi) v[q] = g[vidx<TRANS>(gi, gj, ld)];
-                else if (gj == gi) v[q] = UNIT ? T(1) : g[vidx<TRANS>(gi, gi, ld)];
+                if (gj < gi) v[q] = (T)g[vidx<TRANS>(gi, gj, ld)];
+                else if (gj == gi) v[q] = UNIT ? T(1) : (T)g[vidx<TRANS>(gi, gi, ld)];
                 else v[q] = T(0);
             } else {
                 v[q] = (gi == gj) ? T(1) : T(0);
@@ -180,9 +189,11 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
         for (int q = 0; q < 32; ++q) {
             const int r = TRANS ? q : lane, c = TRANS ? lane : q;
             tp[r * TP + c] = v[q];
+            tmax = fmaxf(tmax, fabsf((float)v[q]));
         }
     }
     __syncthreads();
+    if (tau > 0.f) atomicMax(&s_tmax, __float_as_uint(tmax));   // non-negative: bit order = value order
 
     // Planes of T itself (diagonal blocks of the mixed path), before inverting.
     if (q0 != nullptr) {
@@ -197,10 +208,33 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             atomicMin(info, info_as >= 0 ? info_as : (row0 >= 0 ? (long long)(row0 + bad) : (long long)d.index));
     }
 
+    if constexpr (std::is_same<T, float>::value) {
+        if (tau > 0.f) {
+            float xmax = 0.f;
+            for (int x = tid; x < ntl * 1024; x += NT) {
+                const int tl = x / 1024, e = x % 1024;
+                xmax = fmaxf(xmax, fabsf(tiles[(size_t)tl * TE + (e / 32) * TP + e % 32]));
+            }
+            atomicMax(&s_xmax, __float_as_uint(xmax));
+            __syncthreads();
+            const float growth = __uint_as_float(s_xmax) * __uint_as_float(s_tmax);
+            __syncthreads();
+            if (!(growth <= tau) && n <= 128) {
+                // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
+                // the shared memory of the FP32 block
+                double *dt = reinterpret_cast<double *>(tiles);
+                invert_block<double, TRANS, UNIT, 4, NT, float>(d, dt, dt + (size_t)BLimits<4>::kTiles * TE, info,
+                                                                row0, nullptr, nullptr, nullptr, 0, ntot, nullptr,
+                                                                nullptr, nullptr, info_as, 0.f);
+                return;
+            }
+        }
+    }
+
     // Store the lower triangle back (unit diagonal not written), one warp per tile;
     // off-diagonal tiles inside the block as float4 stores when the source allowed
     // float4 loads.
-    T *go = reinterpret_cast<T *>(d.ptr);
+    S *go = reinterpret_cast<S *>(d.ptr);
     for (int tl = warp; tl < ntl; tl += nwarps) {
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= tl) ++I;
@@ -227,14 +261,15 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
         for (int q = 0; q < 32; ++q) {
             const int r = TRANS ? q : lane, c = TRANS ? lane : q;
             const int gi = I * 32 + r, gj = J * 32 + c;
-            if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = tp[r * TP + c];
+            if (gi < n && gj < n && gj <= gi && !(UNIT && gi == gj)) go[vidx<TRANS>(gi, gj, ld)] = (S)tp[r * TP + c];
         }
     }
     if (p0 != nullptr) write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
 }
 
 template <typename T, bool TRANS, bool UNIT, int MAXT, int NT>
-__global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict__ descs, int count, int *counter, long long *info) {
+__global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict__ descs, int count, int *counter, long long *info,
+                                                        const float *tau_ptr) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     T *tiles = reinterpret_cast<T *>(smem_raw);
     T *wt = tiles + (size_t)BLimits<MAXT>::kTiles * TE;
@@ -246,7 +281,8 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict_
         const int job = s_job;
         __syncthreads();
         if (job >= count) break;
-        invert_block<T, TRANS, UNIT, MAXT, NT>(descs[job], tiles, wt, info, -1, nullptr, nullptr, nullptr, 0, 0);
+        invert_block<T, TRANS, UNIT, MAXT, NT>(descs[job], tiles, wt, info, -1, nullptr, nullptr, nullptr, 0, 0,
+                                               nullptr, nullptr, nullptr, -1, tau_ptr ? *tau_ptr : 0.f);
         __syncthreads();
     }
 }
@@ -282,7 +318,7 @@ size_t smem_bytes() {
     return (size_t)(BLimits<MAXT>::kTiles + BLimits<MAXT>::kWTiles) * TE * sizeof(T);
 }
 
-using KernFn = void (*)(const BDesc *, int, int *, long long *);
+using KernFn = void (*)(const BDesc *, int, int *, long long *, const float *);
 
 template <typename T, int MAXT, int NT>
 KernFn pick3(bool trans, bool unit) {
@@ -337,6 +373,7 @@ struct tri_batched_plan {
     bool trans = false, unit = false;
     triinv::BDesc *d_desc = nullptr;   // sorted, largest first
     int *d_counter = nullptr;
+    float *d_tau = nullptr;            // growth limit of the FP64 fallback (device, FP32 plans)
     int threads = 512;
     int ctas = 0;
     size_t smem = 0;
@@ -349,6 +386,8 @@ namespace triinv {
 namespace {
 
 int max_block(tri_dtype dt) { return dt == TRI_F64 ? 128 : 256; }
+
+constexpr float kDefaultGrowthLimit = 1.0e4f;   // FP32 batches: max|X| max|T| beyond it -> FP64
 
 // Dynamic shared memory above 48 KB must be allowed per kernel before any launch (and
 // before stream capture).
@@ -368,7 +407,7 @@ cudaError_t launch_plan_kernel(const tri_batched_plan *p, cudaStream_t s, long l
     KernFn k = pick_kernel(p->dtype, p->trans, p->unit, threads, &smem);
     cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k<<<p->ctas, threads, smem, s>>>(p->d_desc, p->count, p->d_counter, info);
+    k<<<p->ctas, threads, smem, s>>>(p->d_desc, p->count, p->d_counter, info, p->d_tau);
     return cudaGetLastError();
 }
 
@@ -491,10 +530,20 @@ tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *co
         p->flops += (double)sizes[i] * sizes[i] * sizes[i] / 3.0;
     }
     p->count = (int)hd.size();
-    if (cudaMalloc(&p->d_counter, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&p->d_counter, sizeof(int)) != cudaSuccess || cudaMalloc(&p->d_tau, sizeof(float)) != cudaSuccess) {
+        cudaFree(p->d_counter);
         delete p;
         cudaGetLastError();
         return TRI_ERR_NOMEM;
+    }
+    {
+        const float tau = p->dtype == TRI_F32 ? kDefaultGrowthLimit : 0.f;
+        if (cudaMemcpy(p->d_tau, &tau, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(p->d_counter);
+            cudaFree(p->d_tau);
+            delete p;
+            return TRI_ERR_CUDA;
+        }
     }
     if (p->count > 0) {
         if (cudaMalloc(&p->d_desc, sizeof(BDesc) * hd.size()) != cudaSuccess) {
@@ -550,8 +599,18 @@ tri_status tri_batched_plan_destroy(tri_batched_plan *plan) {
     if (plan->graph) cudaGraphDestroy(plan->graph);
     cudaFree(plan->d_desc);
     cudaFree(plan->d_counter);
+    cudaFree(plan->d_tau);
     delete plan;
     return TRI_OK;
+}
+
+tri_status tri_batched_plan_set_growth_limit(tri_batched_plan *plan, double tau) {
+    if (!plan || tau != tau) return TRI_ERR_ARG;
+    if (plan->dtype != TRI_F32) return TRI_ERR_UNSUPPORTED;
+    const float t = tau > 0.0 ? (float)std::min(tau, 3.0e38) : 0.f;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return TRI_ERR_ARG;
+    return cudaMemcpy(plan->d_tau, &t, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 
 int tri_batched_plan_threads(const tri_batched_plan *plan) { return plan ? plan->threads : 0; }

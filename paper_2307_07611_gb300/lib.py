@@ -62,6 +62,7 @@ def _declare(lib):
         "tri_batched_exec": ([vp, vp], i32),
         "tri_batched_plan_destroy": ([vp], i32),
         "tri_batched_plan_threads": ([vp], i32),
+        "tri_batched_plan_set_growth_limit": ([vp, ctypes.c_double], i32),
         "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
         "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
@@ -190,6 +191,10 @@ def tri_batched_plan_destroy(plan) -> int:
 
 def tri_batched_plan_threads(plan) -> int:
     return load().tri_batched_plan_threads(plan)
+
+
+def tri_batched_plan_set_growth_limit(plan, tau) -> int:
+    return load().tri_batched_plan_set_growth_limit(plan, float(tau))
 
 
 def tri_inv_batched(count, sizes, ptrs, uplo, diag, dtype, stream=0) -> int:

@@ -188,3 +188,7 @@ def test_sqr_argument_errors_need_no_gpu(libtri):
     assert lib.sqr_inv(-1, 4096, 1, lib.TRI_F32) == A
     assert lib.sqr_inv(0, 0, 1, lib.TRI_F32) == lib.TRI_OK
     assert lib.sqr_inv(4, 0, 4, lib.TRI_F32) == A
+
+
+def test_batched_growth_limit_null_plan_needs_no_gpu(libtri):
+    assert lib.tri_batched_plan_set_growth_limit(None, 1e4) == lib.TRI_ERR_ARG

@@ -164,3 +164,77 @@ def test_batched_rejects_large_blocks(lib):
     assert lib.tri_inv_batched(1, [300], [buf.data_ptr()], 0, 0, lib.TRI_F32, 0) == lib.TRI_ERR_UNSUPPORTED
     assert lib.tri_inv_batched(1, [129], [buf.data_ptr()], 0, 0, lib.TRI_F64, 0) == lib.TRI_ERR_UNSUPPORTED
     assert lib.tri_inv_batched(0, [], [], 0, 0, lib.TRI_F32, 0) == lib.TRI_OK
+
+
+def _ill_block(n, scale, seed):
+    """Unit-diagonal lower block with strict lower entries N(0,1) * scale: growth
+    max|X| max|T| far above 1e4 at the sizes used (measured on the host: n = 96,
+    scale 0.6 gives 1.2e6), while a plain FP32 recurrence loses digits in the small
+    entries of X."""
+    g = np.random.default_rng(seed)
+    return np.eye(n) + np.tril(g.standard_normal((n, n)), -1) * scale
+
+
+def _run_plan(lib, blocks, tau, unit):
+    b = Batch(blocks, True, "f32")
+    sizes = [t.shape[0] for t in blocks]
+    st, plan = lib.tri_batched_plan_create(len(blocks), sizes, b.ptrs, lib.TRI_LOWER,
+                                           lib.TRI_UNIT if unit else lib.TRI_NONUNIT, lib.TRI_F32)
+    assert st == lib.TRI_OK
+    if tau is not None:
+        assert lib.tri_batched_plan_set_growth_limit(plan, tau) == lib.TRI_OK
+    assert lib.tri_batched_exec(plan, int(torch.cuda.current_stream().cuda_stream)) == lib.TRI_OK
+    torch.cuda.synchronize()
+    assert lib.tri_batched_plan_destroy(plan) == lib.TRI_OK
+    return b.result(unit)
+
+
+def _entry_rel_err(x, t):
+    want = oracle.tri_inv(t.astype(np.float32).astype(np.float64), lower=True, unit=True)
+    m = np.tril(np.ones(t.shape, bool), -1) & (want != 0)
+    return np.max(np.abs(x[m] - want[m]) / np.abs(want[m]))
+
+
+def test_batched_growth_limit_fp64_leaf(lib):
+    """An FP64 leaf only for ill-conditioned blocks: with the default limit (1e4) a block of
+    order <= 128 whose FP32 inverse shows growth above it is inverted again in FP64, so every
+    entry is within one FP32 rounding of the FP64 oracle (2^-24 relative, plus FP64 error);
+    with the limit disabled the FP32 recurrence is measurably worse on the same block."""
+    blocks = [_ill_block(96, 0.6, 3), _ill_block(64, 1.0, 4)]
+    on = _run_plan(lib, blocks, None, True)
+    off = _run_plan(lib, blocks, 0.0, True)
+    for x_on, x_off, t in zip(on, off, blocks):
+        e_on, e_off = _entry_rel_err(x_on, t), _entry_rel_err(x_off, t)
+        assert e_on <= 2.0 ** -23, e_on
+        assert e_off > 10 * e_on, (e_off, e_on)
+    assert lib.tri_get_info()[0] == lib.TRI_OK
+
+
+def test_batched_growth_limit_power_of_two_block(lib):
+    """Subdiagonal -2 (x_ij = 2^(i-j), growth 2^(n-1)): the FP64 leaf runs and the result is
+    exact."""
+    n = 64
+    t = np.eye(n) - 2.0 * np.eye(n, k=-1)
+    (x,) = _run_plan(lib, [t], None, False)
+    want = np.tril(2.0 ** (np.arange(n)[:, None] - np.arange(n)[None, :]))
+    assert np.array_equal(x, want)
+
+
+def test_batched_growth_limit_leaves_the_rest_alone(lib):
+    """Well-conditioned blocks (the batched law) and blocks above 128 rows keep the FP32
+    result: bit-identical with the limit on and off."""
+    blocks = [inputs.tri_lower(n, seed=n).astype(np.float64) for n in (40, 128, 200)]
+    blocks.append(_ill_block(200, 0.5, 7))
+    on = _run_plan(lib, blocks, None, False)
+    off = _run_plan(lib, blocks, 0.0, False)
+    for a, b in zip(on, off):
+        assert np.array_equal(a, b)
+
+
+def test_batched_growth_limit_errors(lib):
+    buf = torch.zeros(64 * 64, dtype=torch.float64, device="cuda")
+    st, plan = lib.tri_batched_plan_create(1, [64], [buf.data_ptr()], lib.TRI_LOWER, lib.TRI_UNIT, lib.TRI_F64)
+    assert st == lib.TRI_OK
+    assert lib.tri_batched_plan_set_growth_limit(plan, 10.0) == lib.TRI_ERR_UNSUPPORTED
+    assert lib.tri_batched_plan_set_growth_limit(plan, float("nan")) == lib.TRI_ERR_ARG
+    assert lib.tri_batched_plan_destroy(plan) == lib.TRI_OK
