@@ -299,9 +299,18 @@ def _secondary_rest(torch, lib, dev, out, only):
     lib.check(st, "tri_batched_plan_create")
     ms = event_time(torch, lambda: lib.check(lib.tri_batched_exec(plan, sh)), 10, 3, setup=lambda: wk.copy_(pr))
     fl = float(sum(float(k) ** 3 / 3 for k in sizes))
+    # baseline: the same blocks by a loop of plain tri_inv_ex calls (caller workspace)
+    need = max(lib.tri_inv_workspace_size(int(k), lib.TRI_F32) for k in sizes)
+    wsb = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    wp = (wsb.data_ptr() + 255) // 256 * 256
+    def loop():
+        for k, ptr in zip(sizes, ptrs):
+            lib.check(lib.tri_inv_ex(0, 0, int(k), ptr, int(k), lib.TRI_F32, wp, need, sh))
+    loop_ms = event_time(torch, loop, 1, 1, setup=lambda: wk.copy_(pr))
     out["batched_4096"] = {"value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (sum n^3/3)", "ms": ms,
                            "threads": lib.tri_batched_plan_threads(plan),
-                           "dense_bytes_GBps": 2 * host.nbytes / (ms * 1e-3) / 1e9}
+                           "dense_bytes_GBps": 2 * host.nbytes / (ms * 1e-3) / 1e9,
+                           "loop_of_tri_inv_ms": loop_ms}
     lib.tri_batched_plan_destroy(plan)
     del pr, wk
     return _secondary_adjoint(torch, lib, dev, out, only)
