@@ -407,7 +407,11 @@ def _secondary_factor(torch, lib, dev, out, only):
                 [lu[:c, c].double(), torch.ones(1, dtype=torch.float64, device=dev)])
             ac = pr.T[:, c].double()
             errs.append(float((col - ac).norm() / ac.norm()))
-        res[name] = {"ms": ms, "value": 4 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "lu_column_err_max": max(errs)}
+        # growth factor of the LU (max |U| / max |A| with the Doolittle U = diag(L) U_Crout)
+        rowmax = torch.clamp(torch.triu(lu, 1).abs().amax(dim=1), min=1.0)
+        growth = float((lu.diagonal().abs() * rowmax).max() / pr.abs().max())
+        res[name] = {"ms": ms, "value": 4 * n ** 3 / 3 / (ms * 1e-3) / 1e12, "lu_column_err_max": max(errs),
+                     "lu_growth_factor": growth}
         del ws
     res["unit"] = "TFLOP/s (4n^3/3 executed: LU plus both inverse factors)"
     out[f"skul_f32_n{n}"] = res
