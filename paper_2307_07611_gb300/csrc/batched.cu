@@ -209,7 +209,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     }
 
     if constexpr (std::is_same<T, float>::value) {
-        if (tau > 0.f) {
+        if (tau > 0.f && n <= 128) {   // larger blocks keep the FP32 result: no scan
             float xmax = 0.f;
             for (int x = tid; x < ntl * 1024; x += NT) {
                 const int tl = x / 1024, e = x % 1024;
@@ -219,7 +219,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             __syncthreads();
             const float growth = __uint_as_float(s_xmax) * __uint_as_float(s_tmax);
             __syncthreads();
-            if (!(growth <= tau) && n <= 128) {
+            if (!(growth <= tau)) {
                 // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
                 // the shared memory of the FP32 block
                 double *dt = reinterpret_cast<double *>(tiles);
