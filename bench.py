@@ -645,7 +645,9 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3-split, f32 accumulate" if mode == "mixed" else "f32",
+            "dtype": "bf16" if mode == "mixed" else "f32",
+            "dtype_detail": ("split-BF16 tensor-core products (3 terms; 6 for the residual), FP32 "
+                             "accumulate, FP32 diagonal blocks" if mode == "mixed" else "FP32 FFMA"),
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "mode": mode, "leaf": 64,
                        "parallelism": f"replicas x{world}",
