@@ -443,20 +443,20 @@ tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, i
                void *stream) {
     if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
-    cudaStream_t st_ = (cudaStream_t)stream;
+    cudaStream_t cs = (cudaStream_t)stream;
     if (!a || !r || !s || lda < n || ldr < n || lds < n) return TRI_ERR_ARG;
     if (n > 65535) return TRI_ERR_UNSUPPORTED;
     Ctx c;
-    tri_status st = device_ctx(st_, &c);
+    tri_status st = device_ctx(cs, &c);
     if (st != TRI_OK) return st;
     const size_t need = sqr_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, st_) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, need, cs) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
     st = sqr_ex(n, a, lda, r, ldr, s, lds, dtype, ws, need, stream);
-    cudaError_t e = cudaFreeAsync(ws, st_);
+    cudaError_t e = cudaFreeAsync(ws, cs);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
 }
@@ -466,18 +466,18 @@ tri_status sqr_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *strea
     if (n == 0) return TRI_OK;
     if (!a || lda < n) return TRI_ERR_ARG;
     if (n > 65535) return TRI_ERR_UNSUPPORTED;
-    cudaStream_t st_ = (cudaStream_t)stream;
+    cudaStream_t cs = (cudaStream_t)stream;
     Ctx c;
-    tri_status st = device_ctx(st_, &c);
+    tri_status st = device_ctx(cs, &c);
     if (st != TRI_OK) return st;
     const size_t need = sqr_inv_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, st_) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, need, cs) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
     st = run_sqr_inv(c, dtype, n, a, lda, ws);
-    cudaError_t e = cudaFreeAsync(ws, st_);
+    cudaError_t e = cudaFreeAsync(ws, cs);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
 }
