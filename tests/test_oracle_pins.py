@@ -219,6 +219,31 @@ def test_crit_star_counts_match_paper(n):
     assert np.abs(s - oracle.tri_inv(t, lower=False, unit=True)).max() < 1e-12
 
 
+@pytest.mark.parametrize("n", [3, 6, 11])
+def test_bordered_block_inverse(n):
+    # Section 3, proof of the main Theorem: [R v; 0 1]^-1 = [S -S v; 0 1] with S = R^-1
+    g = np.random.default_rng(20 + n)
+    r = np.triu(g.uniform(-1, 1, (n, n)), 1) + np.eye(n)
+    v = g.uniform(-1, 1, n)
+    big = np.zeros((n + 1, n + 1))
+    big[:n, :n] = r
+    big[:n, n] = v
+    big[n, n] = 1.0
+    s = oracle.tri_inv(r, lower=False, unit=True)
+    x = oracle.tri_inv(big, lower=False, unit=True)
+    assert np.allclose(x[:n, :n], s, rtol=0, atol=1e-13)
+    assert np.allclose(x[:n, n], -s @ v, rtol=0, atol=1e-13)
+    assert x[n, n] == 1.0 and not np.any(x[n, :n])
+
+
+@pytest.mark.parametrize("m", range(2, 12))
+def test_combrit_star_total_count_closed_form(m):
+    # Section 4.1: sum_{j=2}^{m} (m - j + 1)(j + 2) 2^(j-3) = m/2 (2^m - 2), in exact integers
+    # (times 2 to clear the 2^-1 of j = 2)
+    lhs2 = sum((m - j + 1) * (j + 2) * 2 ** (j - 2) for j in range(2, m + 1))
+    assert lhs2 == m * (2 ** m - 2)
+
+
 def test_crit_total_flops_small_values():
     f = lambda m: (m ** 3 - 3 * m ** 2 + 8 * m - 3) // 3
     assert f(3) == 7 and f(4) == 15
