@@ -143,6 +143,22 @@ def test_sqr_inv_parity(lib, dt, n):
     assert residual(a, x) <= (1e-13 if dt == "f64" else 5e-6)
 
 
+def test_sqr_inv_mixed_tensor_core_product(lib):
+    """n = 2048: the final S Q^T (upper S, transposed Q) has enough output tiles to run on
+    the tensor cores directly."""
+    n = 2048
+    a = inputs.general(n, seed=21, dtype=np.float32).astype(np.float64)
+    dev = torch.from_numpy(np.ascontiguousarray(a.T).astype(np.float32)).cuda()
+    st = lib.sqr_inv(n, dev.data_ptr(), n, lib.TRI_F32_MIXED, int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert st == lib.TRI_OK and lib.tri_get_info()[0] == lib.TRI_OK
+    x = dev.cpu().numpy().T.astype(np.float64)
+    q, r, s = oracle.sqr(a)
+    want = s @ q.T
+    assert np.abs(x - want).max() / np.abs(want).max() <= 8 * tol(n, "mixed")
+    assert residual(a, x) <= 5e-6
+
+
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_sqr_inv_needs_no_pivoting(lib, dt):
     """A zero leading entry stops the unpivoted LU of gen_inv; the QR route inverts it."""
