@@ -68,6 +68,27 @@ def max_over_ranks(torch, dist, local_ms: float, world: int, device) -> float:
     return float(t.item())
 
 
+# Rank layout of the running job (set by main); the batched and adjoint workloads shard
+# their independent blocks / matrices over it, the others run one replica per rank.
+JOB = {"rank": 0, "world": 1, "dist": None}
+
+
+def owned_blocks(lib, sizes, rank: int, world: int):
+    """Indices of the blocks this rank inverts: the library's host-side partition of the
+    batch (longest first to the least-loaded rank by m^3), the same on every rank."""
+    if world <= 1:
+        return list(range(len(sizes)))
+    owner, _ = lib.tri_batched_partition(sizes, world)
+    return [i for i, r in enumerate(owner) if r == rank]
+
+
+def owned_range(count: int, rank: int, world: int):
+    """Contiguous share [lo, hi) of `count` equal-size matrices (a strided batch)."""
+    per, extra = divmod(count, world)
+    lo = rank * per + min(rank, extra)
+    return lo, lo + per + (1 if rank < extra else 0)
+
+
 def aggregate_value(world: int, flops_per_step: float, steps: int, max_ms: float) -> float:
     """Whole-job throughput (TFLOP/s): the work of all ranks over the slowest rank's time
     (replicas: every rank runs the same per-rank workload)."""
@@ -102,6 +123,22 @@ def load_peaks():
         return PEAKS_FALLBACK, "fallback"
 
 
+_ALU = {}
+
+
+def measured_alu_peaks(lib):
+    """FFMA and DFMA peaks of this GPU measured by the library's own FMA-chain kernel
+    (tri_alu_peak: full grid, 8 independent dependent chains per thread, CUDA events),
+    once per process: the denominators of the CUDA-core ("alu") rooflines."""
+    if not _ALU:
+        f32, ms32 = lib.tri_alu_peak(lib.TRI_F32, 1 << 18)
+        f64, ms64 = lib.tri_alu_peak(lib.TRI_F64, 1 << 15)
+        _ALU.update({"fp32_tflops": f32, "fp64_tflops": f64, "fp32_ms": ms32, "fp64_ms": ms64,
+                     "how": "tri_alu_peak: 8 dependent FMA chains per thread, 4 (FP32) / 2 (FP64) CTAs "
+                            "of 512 threads per SM, one timed launch after a warm-up"})
+    return _ALU
+
+
 # ---- CPU oracle timing (reference arm and cpu_baseline) ------------------------------
 
 _T_CACHE = {}
@@ -110,20 +147,23 @@ _T_CACHE = {}
 def oracle_sample(n: int, stride: int, offset: int = 0):
     """Time the FP64 oracle's column recurrence on every `stride`-th column of the
     workload; returns (TFLOP/s in the n^3/3 convention, seconds, threads, sample text).
-    The sample's share of the n^3/3 work is sum_j (n-j)(n-j-1) over the sampled j."""
+    The sample's share of the n^3/3 work is sum_j (n-j)(n-j-1) over the sampled j.
+    The oracle's row-major lower view of T is built once per n, outside the timed
+    interval, so a sample of a few columns is not charged for an O(n^2) copy."""
     import numpy as np
     import oracle
     from paper_2307_07611_gb300 import inputs
 
     if n not in _T_CACHE:
-        _T_CACHE[n] = inputs.tri_lower(n, seed=0, law="normal", dtype=np.float32).astype(np.float64)
-    t = _T_CACHE[n]
+        t = inputs.tri_lower(n, seed=0, law="normal", dtype=np.float32).astype(np.float64)
+        _T_CACHE[n] = oracle.LowerView(t, lower=True)
+    view = _T_CACHE[n]
     cols = np.arange(offset % stride, n, stride, dtype=np.int64)
     w_all = sum((n - j) * (n - j - 1) for j in range(n))
     w_s = float(sum((n - int(j)) * (n - int(j) - 1) for j in cols))
     threads = oracle.max_threads()
     t0 = time.perf_counter()
-    oracle.tri_inv_cols(t, cols, lower=True, threads=threads)
+    view.cols(cols, threads=threads)
     dt = time.perf_counter() - t0
     work = flops_tri(n) * w_s / w_all
     return work / dt / 1e12, dt, threads, f"{len(cols)} of {n} columns (every {stride}th), {w_s / w_all:.3f} of the work"
@@ -248,8 +288,10 @@ def secondary(torch, lib, dev, only=None):
         td = pr.T.tril()
         r = td @ xd
         r.diagonal().sub_(1.0)
-        out["single_f64_n512"] = {"value": n ** 3 / 3 / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (n^3/3)", "ms": ms,
-                                  "residual": float(r.norm() / (td.norm() * xd.norm()))}
+        v = n ** 3 / 3 / (ms * 1e-3) / 1e12
+        out["single_f64_n512"] = {"value": v, "unit": "TFLOP/s (n^3/3)", "ms": ms,
+                                  "residual": float(r.norm() / (td.norm() * xd.norm())),
+                                  "frac_of_measured_dfma": v / measured_alu_peaks(lib)["fp64_tflops"]}
     if only is not None and not want("general_f32_n16384"):
         return _secondary_rest(torch, lib, dev, out, only)
 
@@ -288,8 +330,13 @@ def _secondary_rest(torch, lib, dev, out, only):
     if not want("batched_4096"):
         return _secondary_adjoint(torch, lib, dev, out, only)
 
-    # batched: 4096 lower FP32 blocks, sizes U{16..256}, one persistent graph-captured launch
-    sizes, blocks = inputs.batched_blocks(4096, seed=0, dtype=np.float32)
+    # batched: 4096 lower FP32 blocks, sizes U{16..256}, one persistent graph-captured launch;
+    # with several ranks each inverts its share of the blocks (no collective)
+    rank, world, dist = JOB["rank"], JOB["world"], JOB["dist"]
+    sizes_all, blocks_all = inputs.batched_blocks(4096, seed=0, dtype=np.float32)
+    mine = owned_blocks(lib, sizes_all, rank, world)
+    sizes = [int(sizes_all[i]) for i in mine]
+    blocks = [blocks_all[i] for i in mine]
     host = np.concatenate([b.T.reshape(-1) for b in blocks]).astype(np.float32)
     pr = torch.from_numpy(host).to(dev)
     wk = torch.empty_like(pr)
@@ -297,20 +344,27 @@ def _secondary_rest(torch, lib, dev, out, only):
     ptrs = [wk.data_ptr() + 4 * int(o) for o in offs]
     st, plan = lib.tri_batched_plan_create(len(sizes), sizes, ptrs, 0, 0, lib.TRI_F32)
     lib.check(st, "tri_batched_plan_create")
-    ms = event_time(torch, lambda: lib.check(lib.tri_batched_exec(plan, sh)), 10, 3, setup=lambda: wk.copy_(pr))
-    fl = float(sum(float(k) ** 3 / 3 for k in sizes))
-    # baseline: the same blocks by a loop of plain tri_inv_ex calls (caller workspace)
-    need = max(lib.tri_inv_workspace_size(int(k), lib.TRI_F32) for k in sizes)
-    wsb = torch.empty(need + 256, dtype=torch.uint8, device=dev)
-    wp = (wsb.data_ptr() + 255) // 256 * 256
-    def loop():
-        for k, ptr in zip(sizes, ptrs):
-            lib.check(lib.tri_inv_ex(0, 0, int(k), ptr, int(k), lib.TRI_F32, wp, need, sh))
-    loop_ms = event_time(torch, loop, 1, 1, setup=lambda: wk.copy_(pr))
-    out["batched_4096"] = {"value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (sum n^3/3)", "ms": ms,
-                           "threads": lib.tri_batched_plan_threads(plan),
-                           "dense_bytes_GBps": 2 * host.nbytes / (ms * 1e-3) / 1e9,
-                           "loop_of_tri_inv_ms": loop_ms}
+    ms_rank = event_time(torch, lambda: lib.check(lib.tri_batched_exec(plan, sh)), 10, 3,
+                         setup=lambda: wk.copy_(pr))
+    ms = max_over_ranks(torch, dist, ms_rank, world, dev)
+    fl = float(sum(float(k) ** 3 / 3 for k in sizes_all))
+    res = {"value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (sum n^3/3 over all 4096 blocks)", "ms": ms,
+           "threads": lib.tri_batched_plan_threads(plan), "n_gpus": world,
+           "dense_bytes_GBps": 2 * 4 * float(sum(float(k) ** 2 for k in sizes_all)) / (ms * 1e-3) / 1e9}
+    if world > 1:
+        res.update({"scaling": "strong", "parallelism": f"blocks partitioned over {world} ranks, no collective",
+                    "blocks_on_rank0": len(mine), "rank0_ms": ms_rank})
+    else:
+        # baseline: the same blocks by a loop of plain tri_inv_ex calls (caller workspace)
+        need = max(lib.tri_inv_workspace_size(int(k), lib.TRI_F32) for k in sizes)
+        wsb = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        wp = (wsb.data_ptr() + 255) // 256 * 256
+
+        def loop():
+            for k, ptr in zip(sizes, ptrs):
+                lib.check(lib.tri_inv_ex(0, 0, int(k), ptr, int(k), lib.TRI_F32, wp, need, sh))
+        res["loop_of_tri_inv_ms"] = event_time(torch, loop, 1, 1, setup=lambda: wk.copy_(pr))
+    out["batched_4096"] = res
     lib.tri_batched_plan_destroy(plan)
     del pr, wk
     return _secondary_adjoint(torch, lib, dev, out, only)
@@ -323,9 +377,15 @@ def _secondary_adjoint(torch, lib, dev, out, only):
     if only is not None and only != "adjoint_256x1024":
         return _secondary_combrit(torch, lib, dev, out, only)
 
-    # differentiation: batch 256 of n = 1024 FP32 lower (uniform law), loss sum(W * T^-1)
-    b, n = 256, 1024
-    ts, ws_ = inputs.adjoint_batch(b, n, seed=0)
+    # differentiation: batch 256 of n = 1024 FP32 lower (uniform law), loss sum(W * T^-1);
+    # with several ranks each takes a contiguous share of the matrices (no collective: the
+    # gradients of independent matrices need no reduction)
+    rank, world, dist = JOB["rank"], JOB["world"], JOB["dist"]
+    b_all, n = 256, 1024
+    ts, ws_ = inputs.adjoint_batch(b_all, n, seed=0)
+    lo, hi = owned_range(b_all, rank, world)
+    ts, ws_ = ts[lo:hi], ws_[lo:hi]
+    b = hi - lo
     pr = torch.from_numpy(np.ascontiguousarray(np.transpose(ts, (0, 2, 1)))).to(dev)
     g = torch.from_numpy(np.ascontiguousarray(np.transpose(ws_, (0, 2, 1)))).to(dev)
     wk = torch.empty_like(pr)
@@ -336,9 +396,14 @@ def _secondary_adjoint(torch, lib, dev, out, only):
             0, 0, n, wk.data_ptr(), n, n * n, b, code, sh)), 3, 1, setup=lambda: wk.copy_(pr))
         bms = event_time(torch, lambda: lib.check(lib.tri_inv_backward_strided_batched(
             0, 0, n, wk.data_ptr(), n, n * n, g.data_ptr(), n, n * n, dt.data_ptr(), n, n * n, b, code, sh)), 3, 1)
-        adj[name] = {"forward_ms": fms, "forward_value": b * n ** 3 / 3 / (fms * 1e-3) / 1e12,
-                     "backward_ms": bms, "backward_value": b * 4 * n ** 3 / 3 / (bms * 1e-3) / 1e12,
-                     "unit": "TFLOP/s (n^3/3 forward, 4n^3/3 backward, per matrix)"}
+        fms = max_over_ranks(torch, dist, fms, world, dev)
+        bms = max_over_ranks(torch, dist, bms, world, dev)
+        adj[name] = {"forward_ms": fms, "forward_value": b_all * n ** 3 / 3 / (fms * 1e-3) / 1e12,
+                     "backward_ms": bms, "backward_value": b_all * 4 * n ** 3 / 3 / (bms * 1e-3) / 1e12,
+                     "unit": "TFLOP/s (n^3/3 forward, 4n^3/3 backward, per matrix, all matrices)"}
+    if world > 1:
+        adj.update({"n_gpus": world, "scaling": "strong",
+                    "parallelism": f"matrices split over {world} ranks, no collective"})
     out["adjoint_256x1024"] = adj
     del pr, g, wk, dt
     torch.cuda.empty_cache()
@@ -446,12 +511,22 @@ def main():
         return run_reference(args)
     if args.profile_config:
         import torch
+        import torch.distributed as dist
         from paper_2307_07611_gb300 import lib
-        lib.load()
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         torch.cuda.set_device(dev)
-        print(json.dumps({"profile_config": args.profile_config,
-                          "result": secondary(torch, lib, dev, only=args.profile_config)}), flush=True)
+        if world > 1:
+            dist.init_process_group("nccl")
+        JOB.update(rank=rank, world=world, dist=dist if world > 1 else None)
+        lib.load()
+        res = secondary(torch, lib, dev, only=args.profile_config)
+        if rank == 0:
+            print(json.dumps({"profile_config": args.profile_config, "n_gpus": world, "result": res}), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
         return 0
 
     import numpy as np
@@ -465,6 +540,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         dist.init_process_group("nccl")
+    JOB.update(rank=rank, world=world, dist=dist if world > 1 else None)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib.load()
@@ -564,8 +640,9 @@ def main():
         p_resid = p_err = None
         if not args.no_quality:
             p_resid, p_err, _ = quality(lib.TRI_F32)
+        p_value = flops_tri(n) * max(3, args.steps // 2) / (p_total * 1e-3) / 1e12
         extra["plain_fp32"] = {
-            "value": flops_tri(n) * max(3, args.steps // 2) / (p_total * 1e-3) / 1e12,
+            "value": p_value, "frac_of_measured_ffma": p_value / measured_alu_peaks(lib)["fp32_tflops"],
             "unit": "TFLOP/s", "ms_per_step": p_total / max(3, args.steps // 2),
             "residual": p_resid, "max_rel_err_vs_oracle_cols": p_err}
 
@@ -587,11 +664,9 @@ def main():
             src = f"{peak_src} bf16_tflops_sustained (MEASURED_PEAKS.json)"
         else:
             bound, unit = "alu", "TFLOP/s"
-            props = torch.cuda.get_device_properties(dev)
-            mhz = float(peaks.get("sm_max_mhz", 2070.0))
-            fma_per_clk = 128 if "f32" in name else 2
-            peak = props.multi_processor_count * fma_per_clk * 2 * mhz * 1e6 / 1e12
-            src = f"derived: {props.multi_processor_count} SMs x {fma_per_clk} FMA/clk x 2 x {mhz:.0f} MHz"
+            alu = measured_alu_peaks(lib)
+            peak = alu["fp64_tflops"] if "f64" in name else alu["fp32_tflops"]
+            src = "measured in this run by tri_alu_peak (" + ("DFMA" if "f64" in name else "FFMA") + ")"
         roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": dominant_traffic(name), "peak_source": src,
                 "launches": rec["launches"], "avg_launch_ms": rec["ms"] / rec["launches"],
@@ -656,6 +731,7 @@ def main():
             "residual": resid, "max_rel_err_vs_oracle_cols": err,
             "info_status": st_info,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "alu_peaks": measured_alu_peaks(lib),
             "clocks": clk, "per_step_ms_min": min(per_ms), "per_step_ms_median": statistics.median(per_ms),
             "trace": trace,
             "configs": configs,

@@ -25,11 +25,21 @@
  *     queued (argument errors are detected and returned before anything is queued).
  *   - The caller owns all memory it passes.  The library never frees caller memory.
  *     Internal scratch comes from the `_ex` workspace argument or, in the plain entry
- *     points, from CUDA's stream-ordered allocator (TRI_ERR_NOMEM if that fails).
+ *     points, from the library's own stream-ordered memory pool on the current device
+ *     (created on first use; freed blocks stay cached in it for later calls; the
+ *     device's default pool is not touched).  TRI_ERR_NOMEM if that allocation fails.
  *   - A zero or non-finite pivot (t_ii, or a pivot of the LU in gen_inv) does not stop
- *     the queued work; its index is recorded on the device (smallest index wins) and
- *     reported by tri_get_info().  The result is then unspecified.  No pivoting is done
- *     and there is no small-pivot threshold.
+ *     the queued work; its index is recorded on the device (smallest index wins).  The
+ *     result is then unspecified.  No pivoting is done and there is no small-pivot
+ *     threshold.  Where the index goes:
+ *       * `_ex` entry points with a non-NULL `d_info` (a DEVICE pointer to one int64_t
+ *         that the call owns until its work completes): the call queues a reset of
+ *         *d_info, its kernels record into it, and a last kernel leaves -1 there if no
+ *         pivot was bad.  Nothing else is touched, so calls on different streams with
+ *         their own words do not see each other's pivots.  Read it after the stream
+ *         has reached the end of the call (e.g. cudaStreamSynchronize, or an event).
+ *       * every other call: one status word per device, reported and cleared by
+ *         tri_get_info() -- shared by all streams and host threads using the device.
  *   - Every wait inside a kernel is bounded; a wait that runs out records
  *     TRI_ERR_TIMEOUT, reported by tri_get_info().
  */
@@ -98,10 +108,15 @@ TRI_API tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int
  * queued work completes. */
 TRI_API size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype);
 
-/* tri_inv with caller-provided scratch.  TRI_ERR_NOMEM if ws_bytes is smaller than
- * tri_inv_workspace_size(n, dtype) or `workspace` is not 256-byte aligned. */
+/* tri_inv with caller-provided scratch and an optional per-call status word.
+ * TRI_ERR_NOMEM if ws_bytes is smaller than tri_inv_workspace_size(n, dtype) or
+ * `workspace` is not 256-byte aligned.
+ *   d_info  NULL (pivots go to the device-wide word of tri_get_info) or a device int64_t
+ *           that receives the first bad pivot index, or -1 (see the conventions above).
+ *           A bounded wait that runs out is still reported by tri_get_info. */
 TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
-                      tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
+                              tri_dtype dtype, void *workspace, size_t ws_bytes, int64_t *d_info,
+                              void *stream);
 
 /* ---------------------------------------------------------------------------------
  * General inverse, in place: A <- A^-1 for a dense n x n matrix, as A^-1 = U^-1 L^-1 from
@@ -111,18 +126,22 @@ TRI_API tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, 
  * dominant ones); a zero or non-finite pivot is recorded and reported by tri_get_info.
  *   n     order, n >= 0;  a: device pointer, lda x n column-major;  lda >= max(1, n).
  *   dtype TRI_F64 (DFMA), TRI_F32 (FFMA) or TRI_F32_MIXED (split-BF16 tensor-core
- *         products with three terms and FP32 accumulation, FP32 leaves).
+ *         products with three terms and FP32 accumulation, FP32 leaves; for n >= 512
+ *         followed by one Newton-Schulz step X <- X + X (I - A X) with a six-term
+ *         residual, which brings the result to FP32 accuracy).
  * Errors: TRI_ERR_ARG, TRI_ERR_NOMEM (scratch), TRI_ERR_CUDA.
  * --------------------------------------------------------------------------------- */
 TRI_API tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream);
 
 /* Bytes of 256-byte aligned device scratch gen_inv_ex needs (about 2 n^2 elements, plus
- * the BF16 operand planes of the largest product for TRI_F32_MIXED). */
+ * for TRI_F32_MIXED the BF16 operand planes of the largest product and, for n >= 512, a
+ * copy of A for the Newton-Schulz residual). */
 TRI_API size_t gen_inv_workspace_size(int64_t n, tri_dtype dtype);
 
-/* gen_inv with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+/* gen_inv with caller scratch (TRI_ERR_NOMEM if too small or misaligned) and an optional
+ * per-call status word d_info (as tri_inv_ex). */
 TRI_API tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *workspace,
-                              size_t ws_bytes, void *stream);
+                              size_t ws_bytes, int64_t *d_info, void *stream);
 
 /* ---------------------------------------------------------------------------------
  * SKUL (Algorithm SKUL, Section 5.1): the unpivoted Crout factorisation A = L U together
@@ -147,9 +166,10 @@ TRI_API tri_status skul(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk,
  * recursion, the BF16 planes for TRI_F32_MIXED and n elements for the pivots). */
 TRI_API size_t skul_workspace_size(int64_t n, tri_dtype dtype);
 
-/* skul with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+/* skul with caller scratch (TRI_ERR_NOMEM if too small or misaligned) and an optional
+ * per-call status word d_info (as tri_inv_ex). */
 TRI_API tri_status skul_ex(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype,
-                           void *workspace, size_t ws_bytes, void *stream);
+                           void *workspace, size_t ws_bytes, int64_t *d_info, void *stream);
 
 /* ---------------------------------------------------------------------------------
  * SQR (Algorithm SQR, Section 5.1): A = Q R (Q orthonormal, R upper with a positive
@@ -177,9 +197,10 @@ TRI_API tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, vo
 /* Bytes of 256-byte aligned device scratch sqr_ex needs. */
 TRI_API size_t sqr_workspace_size(int64_t n, tri_dtype dtype);
 
-/* sqr with caller scratch (TRI_ERR_NOMEM if too small or misaligned). */
+/* sqr with caller scratch (TRI_ERR_NOMEM if too small or misaligned) and an optional
+ * per-call status word d_info (as tri_inv_ex). */
 TRI_API tri_status sqr_ex(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds,
-                          tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream);
+                          tri_dtype dtype, void *workspace, size_t ws_bytes, int64_t *d_info, void *stream);
 
 /* General inverse through SQR, in place: A <- A^-1 = S Q^T (Section 5.1, "S Q^t =
  * A^-1").  Same arguments, conditions and errors as gen_inv; scratch (about 3 n^2
@@ -231,6 +252,17 @@ TRI_API tri_status tri_batched_plan_set_growth_limit(tri_batched_plan *plan, dou
 TRI_API tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs,
                                    tri_uplo uplo, tri_diag diag, tri_dtype dtype, void *stream);
 
+/* Partition of a batch over the ranks of a multi-GPU job (host only, no CUDA call).
+ * The blocks are independent, so each rank inverts its own share with no collective.
+ * owner[i] (HOST array of count int32) receives the rank of block i: blocks taken by
+ * decreasing order sizes[i], each given to the rank with the smallest sum of m^3 so far
+ * (cost of the recursive split, Section 4.1: m^3/3 flops), ties to the lower rank.  Every
+ * rank computes the same assignment from the same sizes.  loads (HOST, world doubles, may
+ * be NULL) receives each rank's sum of m^3.
+ * Errors: TRI_ERR_ARG (count < 0, world < 1, null arrays, a negative size). */
+TRI_API tri_status tri_batched_partition(int64_t count, const int64_t *sizes, int world, int32_t *owner,
+                                         double *loads);
+
 /* ---------------------------------------------------------------------------------
  * tri_inv_combrit -- the same in-place inverse by Algorithm COMBRIT (Section 4.1) with
  * `beta` diagonal blocks per recursion level (beta = 2, 4 or 8; beta = 2 is the split of
@@ -274,9 +306,10 @@ TRI_API tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a
 TRI_API tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
                                            int64_t stride, int64_t batch, tri_dtype dtype, void *stream);
 TRI_API size_t tri_inv_strided_batched_workspace_size(int64_t n, int64_t batch, tri_dtype dtype);
+/* d_info: optional per-call status word (as tri_inv_ex; it records the matrix index). */
 TRI_API tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
                                               int64_t stride, int64_t batch, tri_dtype dtype, void *workspace,
-                                              size_t ws_bytes, void *stream);
+                                              size_t ws_bytes, int64_t *d_info, void *stream);
 
 /* ---------------------------------------------------------------------------------
  * Adjoint of X = T^-1 (not in the paper; the plain definition from
@@ -287,8 +320,8 @@ TRI_API tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int6
  * into the `uplo` triangle of dt (the diagonal is set to 0 for TRI_UNIT); the other
  * triangle of dt is not written.  All matrices column-major, device memory; x, g and dt
  * must not overlap.  TRI_F32 / TRI_F64: CUDA-core products; TRI_F32_MIXED: split-BF16
- * tensor-core products (three terms) for n >= 256, one launch per product for a chunk of
- * the batch whose planes fit in 4 GiB.  Scratch: n*n elements per matrix (plus the BF16
+ * tensor-core products (six terms with FP32 promotion, FP32-class accuracy) for n >= 256,
+ * one launch per product for a chunk of the batch whose planes fit in 4 GiB.  Scratch: n*n elements per matrix (plus the BF16
  * planes of one chunk for TRI_F32_MIXED), from the stream-ordered allocator or `_ex`.
  * --------------------------------------------------------------------------------- */
 TRI_API tri_status tri_inv_backward(tri_uplo uplo, tri_diag diag, int64_t n, const void *x, int64_t ldx,
@@ -323,7 +356,12 @@ TRI_API tri_status tri_inv_backward_strided_batched_ex(tri_uplo uplo, tri_diag d
  *     n = 2048.  TRI_F32_MIXED returns TRI_ERR_UNSUPPORTED.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any stream
- *     capture begins on that device.
+ *     capture begins on that device.  The cached address does not survive
+ *     cudaDeviceReset (the library's module is then loaded again elsewhere): do not
+ *     call this entry point after resetting a device it was used on.
+ *   - The limits above follow from tri_inv_workspace_size (leaves of 64 in FP32 and 16
+ *     in FP64, one h x h block per pair of the widest level); a CPU test checks that
+ *     both limits fit the array.
  *   - Every call on a device shares the one array, which keeps the previous call's
  *     contents (no call reads scratch it has not written itself).  Calls whose GPU work
  *     can overlap -- on different streams, or from host threads without ordering -- race
@@ -371,6 +409,20 @@ TRI_API tri_status tri_mixed_schedule_stats(int64_t n, int ctas, double *stats, 
  * out, otherwise TRI_OK with *first_bad_index = -1.  first_bad_index is a host pointer
  * and may be NULL. */
 TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
+
+/* Measured CUDA-core peak of the current device for dtype TRI_F32 (FFMA) or TRI_F64
+ * (DFMA), in TFLOP/s (2 flops per fused multiply-add): every thread of a full grid runs 8
+ * independent chains of `iters` dependent FMAs, timed with CUDA events after a warm-up.
+ * The denominator of the CUDA-core kernels' rooflines (not part of the method; a
+ * measurement aid).  ms (may be NULL) receives the timed launch's duration.  Allocates
+ * and synchronises; do not call during stream capture.
+ * Errors: TRI_ERR_ARG (dtype, iters < 8, null tflops), TRI_ERR_NOMEM, TRI_ERR_CUDA. */
+TRI_API tri_status tri_alu_peak(tri_dtype dtype, int iters, double *tflops, double *ms);
+
+/* Usage of the library's scratch pool on the current device (bytes): in use now, and the
+ * high-water mark since the pool was created or last reset (reset_high != 0 resets it
+ * after reading).  NULL outputs are skipped.  Creates the pool if it does not exist yet. */
+TRI_API tri_status tri_pool_stats(uint64_t *used, uint64_t *used_high, int reset_high);
 
 /* ---------------------------------------------------------------------------------
  * Kernel tracing (host-side bookkeeping, off by default).  While enabled, every kernel

@@ -61,6 +61,12 @@ def _load():
         lib.oracle_tri_inv.restype = i64
         lib.oracle_tri_inv_cols.argtypes = [i32, i32, i64, dp, i64, i64, dp, dp, i32]
         lib.oracle_tri_inv_cols.restype = i64
+        lib.oracle_view_create.argtypes = [i32, i32, i64, dp, i64]
+        lib.oracle_view_create.restype = ctypes.c_void_p
+        lib.oracle_view_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_view_free.restype = None
+        lib.oracle_view_cols.argtypes = [i64, ctypes.c_void_p, i64, dp, dp, i32]
+        lib.oracle_view_cols.restype = i64
         lib.oracle_crout.argtypes = [i64, dp, i64, dp, dp, i32]
         lib.oracle_crout.restype = i64
         lib.oracle_gen_inv.argtypes = [i64, dp, i64, dp, i64, i32]
@@ -126,6 +132,48 @@ def tri_inv_cols(t, cols, lower: bool = True, unit: bool = False, threads: int =
                                       len(c), c.ctypes.data, out.ctypes.data, threads)
     _check(bad)
     return out
+
+
+class LowerView:
+    """The oracle's row-major lower view of a triangular T, built once; ``cols`` then runs
+    the column recurrence of ``tri_inv_cols`` for any set of columns without rebuilding it
+    (the same arithmetic; only the preparation is shared between requests)."""
+
+    def __init__(self, t, lower: bool = True, unit: bool = False):
+        tc = _f64_colmajor(t)
+        self.n = tc.shape[0]
+        self._lib = _load()
+        self._r = self._lib.oracle_view_create(0 if lower else 1, 1 if unit else 0, self.n, tc.ctypes.data,
+                                               self.n) if self.n else None
+        if self.n and not self._r:
+            raise MemoryError("oracle allocation failed")
+
+    def cols(self, cols, threads: int = 0) -> np.ndarray:
+        c = np.ascontiguousarray(np.asarray(cols, dtype=np.int64))
+        out = np.zeros((self.n, len(c)), dtype=np.float64, order="F")
+        if self.n == 0 or len(c) == 0:
+            return out
+        _check(self._lib.oracle_view_cols(self.n, self._r, len(c), c.ctypes.data, out.ctypes.data, threads))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_r", None):
+            self._lib.oracle_view_free(self._r)
+            self._r = None
+
+
+def inverse_columns(a, cols) -> np.ndarray:
+    """Columns ``cols`` of A^-1 in FP64, straight from the definition: column j is the
+    solution x of A x = e_j.  The solve is LAPACK's (numpy.linalg.solve: LU with partial
+    pivoting, a library primitive), which costs one O(n^3) factorisation for all
+    requested columns; it serves sizes where ``gen_inv`` (plain loops) would take far too
+    long, and is pinned against ``gen_inv`` and the residual ``A x = e_j``."""
+    a64 = np.asarray(a, dtype=np.float64)
+    n = a64.shape[0]
+    c = np.asarray(cols, dtype=np.int64)
+    e = np.zeros((n, len(c)), dtype=np.float64)
+    e[c, np.arange(len(c))] = 1.0
+    return np.linalg.solve(a64, e)
 
 
 def crout(a, threads: int = 0):

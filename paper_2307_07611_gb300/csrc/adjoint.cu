@@ -9,7 +9,7 @@
 //     dT = -tril(M X^T)         (full x upper, lower half of the output: n^3/3)
 // and symmetrically triu for upper T.  Both products go through the generic
 // triangular-aware product (CUDA cores for TRI_F32 / TRI_F64, split-BF16 tensor cores
-// with three terms for TRI_F32_MIXED).
+// with six promoted terms for TRI_F32_MIXED, FP32-class).
 #include <algorithm>
 
 #include "gemm.cuh"
@@ -81,8 +81,9 @@ tri_status run_backward(const Ctx &c, tri_uplo uplo, tri_diag diag, int64_t n, c
     p2.sc = sd;
     cudaError_t e;
     if (dtype == TRI_F32_MIXED && n >= 256) {
-        e = gemm_tc(c, p1, 3, planes, "adj:xtg");
-        if (e == cudaSuccess) e = gemm_tc(c, p2, 3, planes, "adj:mxt");
+        // six promoted terms: the gradient matches the FP32 path's accuracy
+        e = gemm_tc(c, p1, 6, planes, "adj:xtg");
+        if (e == cudaSuccess) e = gemm_tc(c, p2, 6, planes, "adj:mxt");
     } else {
         const tri_dtype d = dtype == TRI_F64 ? TRI_F64 : TRI_F32;
         e = gemm_simt(c, d, p1, "adj:xtg");
@@ -106,7 +107,7 @@ size_t tri_inv_strided_batched_workspace_size(int64_t n, int64_t batch, tri_dtyp
 
 tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
                                       int64_t stride, int64_t batch, tri_dtype dtype, void *workspace,
-                                      size_t ws_bytes, void *stream) {
+                                      size_t ws_bytes, int64_t *d_info, void *stream) {
     if (bad_enums(uplo, diag, dtype) || n < 0 || batch < 0) return TRI_ERR_ARG;
     if (n == 0 || batch == 0) return TRI_OK;
     if (!a || lda < std::max<int64_t>(1, n) || stride < lda * n) return TRI_ERR_ARG;
@@ -117,10 +118,15 @@ tri_status tri_inv_strided_batched_ex(tri_uplo uplo, tri_diag diag, int64_t n, v
     tri_status st = device_ctx_public((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
     const bool trans = uplo == TRI_UPPER, unit = diag == TRI_UNIT;
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
     // Mixed: one launch per product for a whole chunk of matrices (the FP32 levels below
     // the tensor-core size).
-    if (dtype == TRI_F32_MIXED && n > 256) return run_mixed_batched(c, trans, unit, n, (float *)a, lda, stride, batch, workspace);
-    return run_plain_batched(c, dtype == TRI_F64 ? TRI_F64 : TRI_F32, trans, unit, n, a, lda, stride, batch, workspace);
+    if (dtype == TRI_F32_MIXED && n > 256)
+        st = run_mixed_batched(c, trans, unit, n, (float *)a, lda, stride, batch, workspace);
+    else
+        st = run_plain_batched(c, dtype == TRI_F64 ? TRI_F64 : TRI_F32, trans, unit, n, a, lda, stride, batch,
+                               workspace);
+    return info_end(c, d_info, st);
 }
 
 tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, int64_t stride,
@@ -133,11 +139,11 @@ tri_status tri_inv_strided_batched(tri_uplo uplo, tri_diag diag, int64_t n, void
     tri_status st = device_ctx_public(s, &c);
     if (st != TRI_OK) return st;
     void *ws = nullptr;
-    if (need > 0 && cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+    if (need > 0 && lib_malloc_async(&ws, need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
-    st = tri_inv_strided_batched_ex(uplo, diag, n, a, lda, stride, batch, dtype, ws, need, stream);
+    st = tri_inv_strided_batched_ex(uplo, diag, n, a, lda, stride, batch, dtype, ws, need, nullptr, stream);
     if (ws && cudaFreeAsync(ws, s) != cudaSuccess && st == TRI_OK) st = TRI_ERR_CUDA;
     return st;
 }
@@ -177,7 +183,7 @@ tri_status tri_inv_backward_strided_batched(tri_uplo uplo, tri_diag diag, int64_
     if (st != TRI_OK) return st;
     const size_t need = backward_ws(n, batch, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+    if (lib_malloc_async(&ws, need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }

@@ -51,13 +51,6 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
         if (cudaGetSymbolAddress(&pt, g_timeout_word) != cudaSuccess) return TRI_ERR_CUDA;
         if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return TRI_ERR_CUDA;
-        // Keep freed stream-ordered allocations cached in the pool instead of returning
-        // them to the driver, so repeated calls do not pay for fresh allocations.
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-        }
         d.info = (long long *)pi;
         d.timeout = (int *)pt;
         d.ready = true;
@@ -70,9 +63,68 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     return TRI_OK;
 }
 
+// ---- library scratch pool -----------------------------------------------------------
+// Scratch of the allocating entry points comes from a private stream-ordered pool per
+// device, created on the first allocation.  Its release threshold is unlimited, so freed
+// blocks stay cached for the next call; the device's default pool, which other code in
+// the process (PyTorch, the application) may use, is left as it is.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64];
+
+cudaError_t lib_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+// Per-call status word: the caller's d_info is set to "none" before the call's kernels
+// and turned from the internal "none" (LLONG_MAX) into -1 after them.
+__global__ void info_begin_kernel(long long *w) { *w = LLONG_MAX; }
+__global__ void info_end_kernel(long long *w) {
+    if (*w == LLONG_MAX) *w = -1;
+}
+
 }  // namespace
 
 tri_status device_ctx_public(cudaStream_t stream, Ctx *out) { return device_ctx(stream, out); }
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    cudaMemPool_t pool;
+    cudaError_t e = lib_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+tri_status info_begin(Ctx &c, int64_t *d_info) {
+    if (!d_info) return TRI_OK;
+    c.info = (long long *)d_info;
+    info_begin_kernel<<<1, 1, 0, c.stream>>>(c.info);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
+
+tri_status info_end(const Ctx &c, int64_t *d_info, tri_status st) {
+    if (!d_info || st != TRI_OK) return st;
+    info_end_kernel<<<1, 1, 0, c.stream>>>(c.info);
+    return cudaGetLastError() == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+}
 
 namespace {
 
@@ -219,7 +271,7 @@ size_t tri_inv_workspace_size(int64_t n, tri_dtype dtype) {
 }
 
 tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
-                      tri_dtype dtype, void *workspace, size_t ws_bytes, void *stream) {
+                      tri_dtype dtype, void *workspace, size_t ws_bytes, int64_t *d_info, void *stream) {
     if (!valid_enums(uplo, diag, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
     if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
@@ -229,9 +281,12 @@ tri_status tri_inv_ex(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t 
     Ctx c;
     tri_status st = device_ctx((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
     if (dtype == TRI_F32_MIXED)
-        return run_mixed(c, uplo == TRI_UPPER, diag == TRI_UNIT, n, (float *)a, lda, workspace);
-    return run_plain_levels(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, workspace, n);
+        st = run_mixed(c, uplo == TRI_UPPER, diag == TRI_UNIT, n, (float *)a, lda, workspace);
+    else
+        st = run_plain_levels(c, dtype, uplo == TRI_UPPER, diag == TRI_UNIT, n, a, lda, workspace, n);
+    return info_end(c, d_info, st);
 }
 
 tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,
@@ -242,16 +297,11 @@ tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda
     const size_t need = tri_inv_workspace_size(n, dtype);
     void *ws = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
-    if (need > 0) {
-        Ctx c;
-        tri_status st = device_ctx(s, &c);  // sets the pool's release threshold once
-        if (st != TRI_OK) return st;
-        if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
-            cudaGetLastError();
-            return TRI_ERR_NOMEM;
-        }
+    if (need > 0 && lib_malloc_async(&ws, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
     }
-    tri_status st = tri_inv_ex(uplo, diag, n, a, lda, dtype, ws, need, stream);
+    tri_status st = tri_inv_ex(uplo, diag, n, a, lda, dtype, ws, need, nullptr, stream);
     if (ws) {
         cudaError_t e = cudaFreeAsync(ws, s);
         if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
@@ -292,7 +342,7 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
     const size_t mat = ((size_t)ldd * n * es + 255) / 256 * 256;
     const size_t need = tri_inv_workspace_size(n, dtype);
     uint8_t *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, mat + need, s) != cudaSuccess) {
+    if (lib_malloc_async((void **)&buf, mat + need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
@@ -300,7 +350,7 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
     const bool upper = uplo == TRI_UPPER;
     int64_t moved = host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyHostToDevice, s, &e);
     if (e == cudaSuccess) {
-        st = tri_inv_ex(uplo, diag, n, buf, ldd, dtype, need ? buf + mat : nullptr, need, stream);
+        st = tri_inv_ex(uplo, diag, n, buf, ldd, dtype, need ? buf + mat : nullptr, need, nullptr, stream);
         if (st == TRI_OK)
             moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
     }
@@ -323,7 +373,7 @@ tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int
     if (st != TRI_OK) return st;
     const size_t need = combrit_ws_bytes(n, dtype, beta);
     void *ws = nullptr;
-    if (need > 0 && cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+    if (need > 0 && lib_malloc_async(&ws, need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
@@ -338,7 +388,7 @@ size_t gen_inv_workspace_size(int64_t n, tri_dtype dtype) {
 }
 
 tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *workspace, size_t ws_bytes,
-                      void *stream) {
+                      int64_t *d_info, void *stream) {
     if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
     if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;
@@ -348,7 +398,8 @@ tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *wo
     Ctx c;
     tri_status st = device_ctx((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
-    return run_gen_inv(c, dtype, n, a, lda, workspace);
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
+    return info_end(c, d_info, run_gen_inv(c, dtype, n, a, lda, workspace));
 }
 
 tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *stream) {
@@ -361,11 +412,11 @@ tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *strea
     if (st != TRI_OK) return st;
     const size_t need = gen_inv_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+    if (lib_malloc_async(&ws, need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
-    st = gen_inv_ex(n, a, lda, dtype, ws, need, stream);
+    st = gen_inv_ex(n, a, lda, dtype, ws, need, nullptr, stream);
     cudaError_t e = cudaFreeAsync(ws, s);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
@@ -377,7 +428,7 @@ size_t skul_workspace_size(int64_t n, tri_dtype dtype) {
 }
 
 tri_status skul_ex(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype, void *workspace,
-                   size_t ws_bytes, void *stream) {
+                   size_t ws_bytes, int64_t *d_info, void *stream) {
     if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
     if (!a || !sk || lda < n || ldsk < n || a == sk) return TRI_ERR_ARG;
@@ -387,7 +438,8 @@ tri_status skul_ex(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_
     Ctx c;
     tri_status st = device_ctx((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
-    return run_skul(c, dtype, n, a, lda, sk, ldsk, workspace);
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
+    return info_end(c, d_info, run_skul(c, dtype, n, a, lda, sk, ldsk, workspace));
 }
 
 tri_status skul(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dtype dtype, void *stream) {
@@ -401,11 +453,11 @@ tri_status skul(int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, tri_dty
     if (st != TRI_OK) return st;
     const size_t need = skul_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, s) != cudaSuccess) {
+    if (lib_malloc_async(&ws, need, s) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
-    st = skul_ex(n, a, lda, sk, ldsk, dtype, ws, need, stream);
+    st = skul_ex(n, a, lda, sk, ldsk, dtype, ws, need, nullptr, stream);
     cudaError_t e = cudaFreeAsync(ws, s);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
@@ -423,7 +475,7 @@ static bool overlaps(const void *p, int64_t ldp, const void *q, int64_t ldq, int
 }
 
 tri_status sqr_ex(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds, tri_dtype dtype,
-                  void *workspace, size_t ws_bytes, void *stream) {
+                  void *workspace, size_t ws_bytes, int64_t *d_info, void *stream) {
     if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0) return TRI_ERR_ARG;
     if (n == 0) return TRI_OK;
     if (!a || !r || !s || lda < n || ldr < n || lds < n) return TRI_ERR_ARG;
@@ -436,7 +488,8 @@ tri_status sqr_ex(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s
     Ctx c;
     tri_status st = device_ctx((cudaStream_t)stream, &c);
     if (st != TRI_OK) return st;
-    return run_sqr(c, dtype, n, a, lda, r, ldr, s, lds, workspace);
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
+    return info_end(c, d_info, run_sqr(c, dtype, n, a, lda, r, ldr, s, lds, workspace));
 }
 
 tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, int64_t lds, tri_dtype dtype,
@@ -451,11 +504,11 @@ tri_status sqr(int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s, i
     if (st != TRI_OK) return st;
     const size_t need = sqr_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, cs) != cudaSuccess) {
+    if (lib_malloc_async(&ws, need, cs) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
-    st = sqr_ex(n, a, lda, r, ldr, s, lds, dtype, ws, need, stream);
+    st = sqr_ex(n, a, lda, r, ldr, s, lds, dtype, ws, need, nullptr, stream);
     cudaError_t e = cudaFreeAsync(ws, cs);
     if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
     return st;
@@ -472,7 +525,7 @@ tri_status sqr_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *strea
     if (st != TRI_OK) return st;
     const size_t need = sqr_inv_ws_bytes(n, dtype);
     void *ws = nullptr;
-    if (cudaMallocAsync(&ws, need, cs) != cudaSuccess) {
+    if (lib_malloc_async(&ws, need, cs) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }
@@ -498,6 +551,25 @@ tri_status tri_get_info(void *stream, int64_t *first_bad_index) {
     if (first_bad_index) *first_bad_index = (info == LLONG_MAX) ? -1 : (int64_t)info;
     if (tmo) return TRI_ERR_TIMEOUT;
     if (info != LLONG_MAX) return TRI_ERR_SINGULAR;
+    return TRI_OK;
+}
+
+tri_status tri_pool_stats(uint64_t *used, uint64_t *used_high, int reset_high) {
+    cudaMemPool_t pool;
+    if (lib_pool(&pool) != cudaSuccess) return TRI_ERR_CUDA;
+    uint64_t v = 0;
+    if (used) {
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) return TRI_ERR_CUDA;
+        *used = v;
+    }
+    if (used_high) {
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v) != cudaSuccess) return TRI_ERR_CUDA;
+        *used_high = v;
+    }
+    if (reset_high) {
+        v = 0;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v) != cudaSuccess) return TRI_ERR_CUDA;
+    }
     return TRI_OK;
 }
 

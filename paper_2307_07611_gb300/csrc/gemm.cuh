@@ -36,6 +36,8 @@ struct GemmArgs {
     bool split_k = false;                     // FP32 on CUDA cores: allow splitting a long
                                               // k over CTAs (atomic adds, beta == 0 only;
                                               // FP64 always may)
+    double dadd = 0.0;                        // tensor-core path only: added to the diagonal
+                                              // of C after the product (R = I - A X)
 };
 
 double gemm_flops(const GemmArgs &g);
@@ -44,7 +46,9 @@ double gemm_flops(const GemmArgs &g);
 cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name);
 
 // Split-BF16 tensor-core product (FP32 data): both operands are split into BF16
-// hi/mid planes inside `ws` and `terms` (1, 3 or 6) pieces are accumulated in FP32.
+// hi/mid(/lo) planes inside `ws` and `terms` (1, 3 or 6) pieces are accumulated in FP32;
+// six-term products also promote their partial sums to FP32 registers every 64 k, which
+// brings them to about 2^-24 relative (FP32 class).
 // ws must hold gemm_tc_ws_bytes(m, n, k, g.batch) bytes: the operand planes of one chunk
 // of the batch (all matrices of a chunk in one launch).
 size_t gemm_tc_ws_bytes(int64_t m, int64_t n, int64_t k, int64_t batch = 1);

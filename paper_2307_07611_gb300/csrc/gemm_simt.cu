@@ -274,6 +274,7 @@ double gemm_flops(const GemmArgs &g) {
 }
 
 cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char *trace_name) {
+    if (g.dadd != 0.0) return cudaErrorInvalidValue;   // diagonal addend: tensor-core path only
     if (g.m <= 0 || g.n <= 0 || g.batch <= 0 || g.batch2 <= 0) return cudaSuccess;
     if (g.batch * g.batch2 > 65535 || g.m >= (1ll << 31) || g.n >= (1ll << 31) || g.k >= (1ll << 31))
         return cudaErrorInvalidValue;

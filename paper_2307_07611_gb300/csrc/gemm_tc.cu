@@ -2,7 +2,8 @@
 // split-BF16 operands (mixed precision).  Both FP32 operands are split into BF16 planes
 // (x = hi + mid [+ lo]) with the operand's triangle applied, and the requested pieces are
 // accumulated in FP32: 1 term hi*hi, 3 terms hi*hi + hi*mid + mid*hi (about 2^-16
-// relative), 6 terms adding hi*lo + mid*mid + lo*hi (about 2^-24).
+// relative), 6 terms adding hi*lo + mid*mid + lo*hi (about 2^-24; all six read from
+// one fused pipeline stage, partial sums promoted to FP32 registers every 64 k).
 // Tile lists depend on the shape and the triangle kinds only and are cached per device.
 #include <algorithm>
 #include <map>
@@ -147,9 +148,11 @@ cudaError_t gemm_tc(const Ctx &c, const GemmArgs &g, int terms, void *ws, const 
         ep.alpha = (float)g.alpha;
         ep.beta = (float)g.beta;
         ep.cmask = g.cmask;
+        ep.dadd = (float)g.dadd;
         ep.xs = g.sc;
-        e = tc::launch_tc(c, tc::MODE_GEN, false, false, ap, three ? 3 : 2, bp, three ? 3 : 2, tt, tl.d_tiles,
-                          tl.d_off, tl.ctas, ep, (double)nb * terms * gemm_flops(g), trace_name);
+        e = tc::launch_tc(c, three ? tc::MODE_GENP : tc::MODE_GEN, false, false, ap, three ? 3 : 2, bp,
+                          three ? 3 : 2, tt, tl.d_tiles, tl.d_off, tl.ctas, ep, (double)nb * terms * gemm_flops(g),
+                          trace_name);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

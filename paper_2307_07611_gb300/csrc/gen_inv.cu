@@ -234,9 +234,11 @@ void depth_sizes(int64_t n, int L, std::vector<int64_t> &sz) {
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 struct GenLayout {
-    size_t ks, temps, planes, total;
+    size_t ks, temps, planes, a0, total;
     std::vector<size_t> depth_off;
 };
+
+constexpr int64_t kTcMin = 512;   // smaller products stay on CUDA cores
 
 // with_ks: the K\S buffer lives in the scratch (gen_inv); SKUL writes it to the caller's.
 GenLayout gen_layout(int64_t n, tri_dtype dt, bool with_ks = true) {
@@ -252,8 +254,13 @@ GenLayout gen_layout(int64_t n, tri_dtype dt, bool with_ks = true) {
     }
     g.temps = o - g.ks;
     g.planes = 0;
-    if (dt == TRI_F32_MIXED) g.planes = al(gemm_tc_ws_bytes(n, n, n));
-    g.total = o + g.planes;
+    g.a0 = 0;
+    if (dt == TRI_F32_MIXED) {
+        g.planes = al(gemm_tc_ws_bytes(n, n, n));
+        // gen_inv's Newton-Schulz step needs the original A (FP32, leading dimension n)
+        if (with_ks && n >= kTcMin) g.a0 = al((size_t)n * n * 4);
+    }
+    g.total = o + g.planes + g.a0;
     return g;
 }
 
@@ -266,11 +273,12 @@ struct GenCtx {
     bool keep = false;   // write L21, U12 and the leaf factors back over A (SKUL)
 };
 
-constexpr int64_t kTcMin = 512;   // smaller products stay on CUDA cores
-
+// Mixed products: three terms (about 2^-16 relative) in gen_inv, whose Newton-Schulz step
+// then restores FP32 accuracy against A; six promoted terms (about 2^-24) in SKUL, whose
+// factors are the result and get no refinement.
 cudaError_t product(const GenCtx &g, const GemmArgs &a, const char *name) {
     if (g.dt == TRI_F32_MIXED && a.m >= kTcMin && a.n >= kTcMin && a.k >= kTcMin)
-        return gemm_tc(*g.c, a, 3, g.ws + g.lay.ks + g.lay.temps, name);
+        return gemm_tc(*g.c, a, g.keep ? 6 : 3, g.ws + g.lay.ks + g.lay.temps, name);
     return gemm_simt(*g.c, g.dt == TRI_F64 ? TRI_F64 : TRI_F32, a, name);
 }
 
@@ -377,15 +385,35 @@ size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt) {
     return gen_layout(n, dt).total;
 }
 
+// TRI_F32_MIXED with n >= kTcMin ends with one Newton-Schulz step on the dense inverse,
+//     R = I - A X     six promoted terms (FP32 class; R is a difference of nearly equal
+//                     quantities, so it needs the full 24 bits of A and X)
+//     X <- X + X R    one term: R is as small as the three-term inverse's residual, so the
+//                     BF16 error of this product is far below FP32 rounding of X
+// which brings the normwise residual from the three-term products' level to FP32 level.
+// R is written over the K\S buffer, which the final product has consumed.
 tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws) {
     GenCtx g{&c, dt, (uint8_t *)ws, gen_layout(n, dt), leaf_size(dt)};
     uint8_t *ks = (uint8_t *)ws;
     const int64_t ldk = n;
-    cudaError_t e = rec(g, (uint8_t *)a, lda, ks, ldk, 0, n, 0);
+    const bool ns = g.lay.a0 > 0;
+    float *a0 = ns ? (float *)(g.ws + g.lay.ks + g.lay.temps + g.lay.planes) : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ns) e = cudaMemcpy2DAsync(a0, n * 4, a, lda * 4, n * 4, n, cudaMemcpyDeviceToDevice, c.stream);
+    if (e != cudaSuccess) return TRI_ERR_CUDA;
+    e = rec(g, (uint8_t *)a, lda, ks, ldk, 0, n, 0);
     if (e != cudaSuccess) return TRI_ERR_CUDA;
     // A^-1 = S K
     e = product(g, GemmArgs{n, n, n, 1.0, ks, ldk, OP_UPPER, ks, ldk, OP_LOWER_UNIT, 0.0, a, lda, OP_FULL},
                 "gen:sk");
+    if (e != cudaSuccess || !ns) return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
+    void *planes = g.ws + g.lay.ks + g.lay.temps;
+    GemmArgs r{n, n, n, -1.0, a0, n, OP_FULL, a, lda, OP_FULL, 0.0, ks, ldk, OP_FULL};
+    r.dadd = 1.0;
+    e = gemm_tc(c, r, 6, planes, "gen:ns_res");
+    if (e != cudaSuccess) return TRI_ERR_CUDA;
+    e = gemm_tc(c, GemmArgs{n, n, n, 1.0, a, lda, OP_FULL, ks, ldk, OP_FULL, 1.0, a, lda, OP_FULL}, 1, planes,
+                "gen:ns_upd");
     return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 

@@ -30,6 +30,17 @@ __host__ __device__ __forceinline__ int64_t vidx(int64_t i, int64_t j, int64_t l
 // Launch context of the calling thread's current device (api.cu).
 tri_status device_ctx_public(cudaStream_t stream, Ctx *out);
 
+// Stream-ordered scratch from the library's private pool of the current device (api.cu);
+// release it with cudaFreeAsync.
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
+// Per-call status word of the _ex entry points (api.cu).  d_info == nullptr keeps the
+// device-wide word of c.  Otherwise info_begin points c.info at the caller's word and
+// queues its reset; info_end queues the conversion of "no bad pivot" to -1 (when st is OK)
+// and returns st.
+tri_status info_begin(Ctx &c, int64_t *d_info);
+tri_status info_end(const Ctx &c, int64_t *d_info, tri_status st);
+
 // ---- tracing (api.cu) -------------------------------------------------------------
 // While tracing is on, TraceScope records a CUDA event pair around the launches made in
 // its lifetime on `stream`, and books the launch's algorithmic flops and bytes.

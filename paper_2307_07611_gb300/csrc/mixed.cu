@@ -11,7 +11,7 @@
 //        X21 = -X_C W      3 terms                              -> X (FP32) and its planes
 // 5. Newton-Schulz step X <- X (2I - T X) = X + X R:
 //        R = I - T X       6 terms (hh, hm, mh, hl, mm, lh) with FP32 promotion of the
-//                          tensor-core partial sums every 256 k: R is a difference of
+//                          tensor-core partial sums every 64 k: R is a difference of
 //                          nearly equal terms and needs ~2^-24 relative accuracy
 //        X += X R          1 term: R is as small as the forward residual (~3e-8
 //                          normwise at n = 8192), so the BF16 error 2^-8 |X R| of the
@@ -21,6 +21,7 @@
 // TRI_MIXED_SCHEDULE=graph).  Tile lists and schedules depend on n only and are built
 // once per (device, n).
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -109,7 +110,34 @@ int64_t chunk_matrices(int64_t n, int64_t batch) {
 struct Launch {
     int first, ctas, off_first;   // tiles from `first`, CTA offsets from `off_first`
     double flops;
+    int bn = tc::BN;              // output tile width the tiles were cut with
 };
+
+// Output tile width of the level products at split half-size h.  A level's products
+// are P = n / 2h pairs of h x h "triangular x full" products; with 128 x 256 tiles the low
+// levels have few tiles (h = 256: 32 tiles for 152 SMs) whose k range sets the launch's
+// length, so narrower tiles spread them over more SMs and shorten the longest tile.
+// TRI_LEVEL_TILE_N="h:bn,..." (bn in {64, 128, 256}) overrides the table, read once.
+int level_tile_n(int64_t h) {
+    static const std::vector<std::pair<int64_t, int>> table = [] {
+        std::vector<std::pair<int64_t, int>> t;
+        if (const char *e = std::getenv("TRI_LEVEL_TILE_N")) {
+            t.clear();
+            long long hh = 0;
+            int bn = 0, used = 0;
+            while (std::sscanf(e, "%lld:%d%n", &hh, &bn, &used) == 2) {
+                if (bn == 64 || bn == 128 || bn == 256) t.push_back({(int64_t)hh, bn});
+                e += used;
+                if (*e != ',') break;
+                ++e;
+            }
+        }
+        return t;
+    }();
+    for (const auto &p : table)
+        if (p.first == h) return p.second;
+    return tc::BN;
+}
 
 struct Plan {
     tc::Tile *d_tiles = nullptr;
@@ -146,7 +174,7 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **ou
     Plan p;
     std::vector<tc::Tile> v;
     std::vector<int> offs;
-    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms) {
+    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms, int bn = tc::BN) {
         // replicate the single-matrix tiles over the batch
         const size_t one_count = v.size() - from;
         for (int64_t b = 1; b < batch; ++b)
@@ -159,26 +187,27 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **ou
         std::vector<int> o;
         const int ctas = part.empty() ? 0 : tc::schedule_lpt(part, terms, sm_count, o);
         std::copy(part.begin(), part.end(), v.begin() + from);
-        Launch l{(int)from, ctas, (int)offs.size(), flops * (double)batch};
+        Launch l{(int)from, ctas, (int)offs.size(), flops * (double)batch, bn};
         for (int x : o) offs.push_back(x);
         if (vec) vec->push_back(l);
         else *one = l;
     };
     for (int64_t h = kDiag; h < n; h *= 2) {
         const int64_t P = level_pairs(n, h);
+        const int bn = level_tile_n(h);   // divides h (h is 256 * 2^s)
         // W = B X_A  (W is h x P*h, pair q in columns [q*h, q*h + h))
         size_t from = v.size();
         double fl = 0.0;
         for (int64_t q = 0; q < P; ++q) {
             const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
             fl += 3.0 * (double)hc * h * (h + 1);
-            for (int64_t tn = 0; tn < h / tc::BN; ++tn)
+            for (int64_t tn = 0; tn < h / bn; ++tn)
                 for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm)
-                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * tc::BN),
-                                         (int)(tn * tc::BN / tc::BK), (int)(h / tc::BK),
-                                         (int)(tm * tc::BM), (int)(q * h + tn * tc::BN)});
+                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * bn),
+                                         (int)(tn * bn / tc::BK), (int)(h / tc::BK),
+                                         (int)(tm * tc::BM), (int)(q * h + tn * bn)});
         }
-        add(&p.w, nullptr, from, fl, 3);
+        add(&p.w, nullptr, from, fl, 3, bn);
         // X21 = -X_C W
         from = v.size();
         fl = 0.0;
@@ -187,13 +216,13 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **ou
             fl += 3.0 * (double)h * hc * (hc + 1);
             for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
                 const int64_t kend = std::min((tm + 1) * tc::BM, hc);
-                for (int64_t tn = 0; tn < h / tc::BN; ++tn)
-                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)c0, 0, (int)(q * h + tn * tc::BN), 0,
+                for (int64_t tn = 0; tn < h / bn; ++tn)
+                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)c0, 0, (int)(q * h + tn * bn), 0,
                                          (int)cdiv(kend, tc::BK), (int)(c0 + tm * tc::BM),
-                                         (int)(a0 + tn * tc::BN)});
+                                         (int)(a0 + tn * bn)});
             }
         }
-        add(&p.x21, nullptr, from, fl, 3);
+        add(&p.x21, nullptr, from, fl, 3, bn);
     }
     // Newton-Schulz: lower x lower products over the whole matrix.
     const double lower_prod = (double)n * (n + 1) * (n + 2) / 3.0;   // 2 * sum_{i>=j} (i-j+1)
@@ -319,14 +348,14 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         ew.os = ps;
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, tc::MODE_W, trans, unit, tp, 3, xp, 3, three, plan->d_tiles + lw.first,
-                          plan->d_off + lw.off_first, lw.ctas, ew, lw.flops, "tc_gemm:w") != cudaSuccess)
+                          plan->d_off + lw.off_first, lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn) != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         ex.xs = stride;
         ex.os = ps;
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, tc::MODE_X21, trans, unit, xp, 3, wp, 2, three, plan->d_tiles + lx.first,
-                          plan->d_off + lx.off_first, lx.ctas, ex, lx.flops, "tc_gemm:x21") != cudaSuccess)
+                          plan->d_off + lx.off_first, lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
     // 5. Newton-Schulz: R = I - T X, then X += X R

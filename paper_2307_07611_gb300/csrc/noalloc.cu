@@ -7,15 +7,18 @@
 // block in the CUDA allocator nor handle an allocation failure in the middle of its
 // work.  For them this entry point runs the same plain TRI_F32 / TRI_F64 inverse as
 // tri_inv(), but the scratch of the level products lives in the fixed device array
-// below instead of coming from cudaMallocAsync.  The caller still passes the matrix.
+// below instead of coming from the library's stream-ordered pool.  The caller still passes
+// the matrix.
 //
 // The array (TRI_NOALLOC_SCRATCH_BYTES) exists on every GPU that loads the library and
 // stays allocated until the process exits.  Host code cannot use the array's name as a
 // device address (in host code it names a host-side stand-in), so the first call on each
 // device looks the address up with cudaGetSymbolAddress, with that device current, and
-// caches it.  Every call on a device shares the array and finds the previous call's
-// contents in it; the inverse writes every scratch element before reading it within a
-// call, so nothing needs clearing.  Calls whose GPU work can overlap race on the array.
+// caches it for the life of the process (the cache does not survive cudaDeviceReset,
+// after which the module is loaded again at another address).  Every call on a device
+// shares the array and finds the previous call's contents in it; the inverse writes every
+// scratch element before reading it within a call, so nothing needs clearing.  Calls
+// whose GPU work can overlap race on the array.
 #include <mutex>
 
 #include "internal.cuh"
@@ -60,6 +63,6 @@ extern "C" tri_status tri_inv_noalloc(tri_uplo uplo, tri_diag diag, int64_t n, v
     void *scratch = nullptr;
     tri_status st = noalloc_scratch(&scratch);
     if (st != TRI_OK) return st;
-    return tri_inv_ex(uplo, diag, n, a, lda, dtype, scratch, (size_t)TRI_NOALLOC_SCRATCH_BYTES,
+    return tri_inv_ex(uplo, diag, n, a, lda, dtype, scratch, (size_t)TRI_NOALLOC_SCRATCH_BYTES, nullptr,
                       stream);
 }

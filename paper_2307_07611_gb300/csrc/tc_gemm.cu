@@ -91,7 +91,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
             if (j < left && (gm > gn || (!UNIT && gm == gn))) ep.x[xo] += __uint_as_float(r[j]);
             xo += xstep;
         }
-    } else if (MODE == MODE_GEN) {
+    } else if (MODE == MODE_GEN || MODE == MODE_GENP) {
         int64_t xo = xb + gm + gn0 * ep.ldx;
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
@@ -99,7 +99,8 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
             const bool low = ep.cmask == 1 || ep.cmask == 3, up = ep.cmask == 2 || ep.cmask == 4;
             const bool keep = j < left && !(low && gn > gm) && !(up && gm > gn);
             if (keep) {
-                const float v = ep.alpha * __uint_as_float(r[j]);
+                float v = ep.alpha * __uint_as_float(r[j]);
+                if (gm == gn) v += ep.dadd;
                 if (ep.cmask >= 3 && gm == gn) ep.x[xo] = 0.f;     // strict triangle: zero diagonal
                 else ep.x[xo] = ep.beta == 0.f ? v : fmaf(ep.beta, ep.x[xo], v);
             }
@@ -150,20 +151,20 @@ __device__ __forceinline__ void store_upd16(const Epi &ep, int64_t xb, int64_t g
 //   fused    true: a stage holds every distinct plane tile the terms read and the MMA
 //            issuer runs all terms on it (each plane crosses L2 once per k-step); false:
 //            a stage holds the A / B pair of one term (loop: chunk, term, k).
-//   promote  MODE_RES: 64-wide k-blocks accumulated in tensor memory before the epilogue
-//            adds them into FP32 registers.  The accumulator truncates every add, so a
-//            product added after the large hi*hi term loses up to one unit in the last
-//            place of the partial sum; the chunk length bounds that loss.
-// R = I - T X reads 3 + 3 planes for 6 terms: fused 32-wide stages (72 KB, 3 deep) halve
-// its L2 traffic; one-term and three-term products keep 64-wide per-term stages (48 KB,
-// 4 deep), which measured faster for them.
+//   promote  MODE_RES, MODE_GENP: 64-wide k-blocks accumulated in tensor memory before
+//            the epilogue adds them into FP32 registers.  The accumulator truncates every
+//            add, so a product added after the large hi*hi term loses up to one unit in
+//            the last place of the partial sum; the chunk length bounds that loss.
+// R = I - T X and the general six-term products read 3 + 3 planes: fused 32-wide stages
+// (72 KB, 3 deep) halve their L2 traffic; one-term and three-term products keep 64-wide
+// per-term stages (48 KB, 4 deep), which measured faster for them.
 struct Cfg {
     int ks;
     bool fused;
     int promote;
 };
 __host__ __device__ constexpr Cfg cfg_for(int mode) {
-    return mode == MODE_RES ? Cfg{32, true, 1} : Cfg{64, false, 0};
+    return (mode == MODE_RES || mode == MODE_GENP) ? Cfg{32, true, 1} : Cfg{64, false, 0};
 }
 
 constexpr int STAGE_BUDGET = 216 * 1024;
@@ -178,15 +179,19 @@ struct Pipe {
     int batched;         // maps are 3-D (batch outermost): loads take the tile's matrix
 };
 
-template <int MODE, bool TRANS, bool UNIT>
+// BNT: columns of an output tile (UMMA N = 256, 128 or 64).  Narrower tiles give the
+// small products of the low split levels more, shorter tiles (more SMs busy, a shorter
+// longest tile); the widest tile moves the fewest operand bytes per flop.
+template <int MODE, bool TRANS, bool UNIT, int BNT>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe pipe,
                const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
                int *gtimeout) {
-    constexpr bool PROMOTE = (MODE == MODE_RES);
+    constexpr bool PROMOTE = (MODE == MODE_RES || MODE == MODE_GENP);
     constexpr Cfg CF = cfg_for(MODE);
     constexpr int KS = CF.ks;
-    constexpr int A_TILE = BM * KS * 2, B_TILE = BN * KS * 2;
+    constexpr int A_TILE = BM * KS * 2, B_TILE = BNT * KS * 2;
+    constexpr uint32_t IDESC = idesc_for(BNT);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int STAGES = pipe.stages;
@@ -234,7 +239,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             // apart; a k-step of 16 = 32 B inside the swizzled row.
             const uint64_t da = smem_desc(sa + kk * 2048, KS * 128, 1024, kSwizzle128);
             const uint64_t db = smem_desc(sb + kk * 32, 16, KS * 16, KS == 64 ? kSwizzle128 : kSwizzle64);
-            tc_mma(d, da, db, kIdesc, accumulate);
+            tc_mma(d, da, db, IDESC, accumulate);
             accumulate = 1;
         }
     };
@@ -338,7 +343,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem_base + a * (uint32_t)BN;
+                    const uint32_t d = tmem_base + a * (uint32_t)BNT;
                     uint32_t accumulate = 0;
                     for (int jj = CF.fused ? 0 : terms.n - 1; jj >= 0 && ok; --jj) {
                         for (int kb = c0; kb < c1 && ok; ++kb) {
@@ -391,13 +396,13 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             const int cb = chunk_blocks(tl);
             const int64_t gm = (int64_t)tl.om + row;
             const int64_t xb = (int64_t)tl.b * ep.xs, ob = (int64_t)tl.b * ep.os;
-            float sum[PROMOTE ? BN / 2 : 1];
+            float sum[PROMOTE ? BNT / 2 : 1];
             if (PROMOTE) {
 #pragma unroll
-                for (int i = 0; i < BN / 2; ++i) sum[i] = 0.f;
+                for (int i = 0; i < BNT / 2; ++i) sum[i] = 0.f;
             }
             // The update reads X: fetch the first 16 columns before the accumulator is ready.
-            const int64_t gcol0 = (int64_t)tl.on + half * (BN / 2);
+            const int64_t gcol0 = (int64_t)tl.on + half * (BNT / 2);
             float xv[MODE == MODE_UPD ? 16 : 1];
             if (MODE == MODE_UPD) load_x16<TRANS, UNIT>(ep, xb, gm, gcol0, *(float(*)[16])xv);
             for (int c0 = tl.kb0; c0 < tl.kb1; c0 += cb, ++lc) {
@@ -407,11 +412,11 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + a * (uint32_t)BN + (uint32_t)(half * (BN / 2)) +
+                const uint32_t taddr = tmem_base + a * (uint32_t)BNT + (uint32_t)(half * (BNT / 2)) +
                                        ((uint32_t)(quarter * 32) << 16);
                 if (PROMOTE) {
 #pragma unroll
-                    for (int q = 0; q < BN / 32; ++q) {
+                    for (int q = 0; q < BNT / 32; ++q) {
                         uint32_t r[16];
                         tmem_ld16(taddr + q * 16, r);
 #pragma unroll
@@ -421,21 +426,21 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     // Software pipeline: the next 16 X values are in flight while the
                     // current ones are added and stored.
 #pragma unroll 1
-                    for (int q = 0; q < BN / 32; ++q) {
+                    for (int q = 0; q < BNT / 32; ++q) {
                         float xn[16];
-                        if (q + 1 < BN / 32)
+                        if (q + 1 < BNT / 32)
                             load_x16<TRANS, UNIT>(ep, xb, gm, gcol0 + (q + 1) * 16, xn);
                         uint32_t r[16];
                         tmem_ld16(taddr + q * 16, r);
                         store_upd16<TRANS, UNIT>(ep, xb, gm, gcol0 + q * 16, *(float(*)[16])xv, r);
-                        if (q + 1 < BN / 32) {
+                        if (q + 1 < BNT / 32) {
 #pragma unroll
                             for (int i = 0; i < 16; ++i) xv[i] = xn[i];
                         }
                     }
                 } else {
 #pragma unroll 1
-                    for (int q = 0; q < BN / 16; ++q) {
+                    for (int q = 0; q < BNT / 16; ++q) {
                         uint32_t r[8];
                         tmem_ld8(taddr + q * 8, r);
                         epilogue_cols<MODE, TRANS, UNIT, 8>(ep, xb, ob, gm, gcol0 + q * 8, r);
@@ -447,11 +452,11 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             }
             if (PROMOTE && ok) {
 #pragma unroll
-                for (int q = 0; q < BN / 32; ++q) {
+                for (int q = 0; q < BNT / 32; ++q) {
                     uint32_t r[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(sum[q * 16 + i]);
-                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, xb, ob, gm, (int64_t)tl.on + half * (BN / 2) + q * 16, r);
+                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, xb, ob, gm, (int64_t)tl.on + half * (BNT / 2) + q * 16, r);
                 }
             }
         }
@@ -469,10 +474,10 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
 
 // ---- host side ------------------------------------------------------------------------
 
-template <int MODE, bool TRANS, bool UNIT>
+template <int MODE, bool TRANS, bool UNIT, int BNT = BN>
 cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Pipe &pipe, const Tile *d_tiles,
                      const int *d_off, int ctas, const Epi &epi) {
-    auto kern = tc_gemm_kernel<MODE, TRANS, UNIT>;
+    auto kern = tc_gemm_kernel<MODE, TRANS, UNIT, BNT>;
     static bool attr_set[64] = {};
     if (!attr_set[c.device]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM_BYTES);
@@ -567,9 +572,11 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes, int na,
                       const Plane *bplanes, int nb, const Terms &terms, const Tile *d_tiles,
                       const int *d_off, int ctas, const Epi &epi, double flops,
-                      const char *trace_name) {
+                      const char *trace_name, int bn) {
     if (ctas <= 0) return cudaSuccess;
     if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
+    // narrow tiles are built for the level products only
+    if (bn != BN && !((bn == 128 || bn == 64) && (mode == MODE_W || mode == MODE_X21))) return cudaErrorInvalidValue;
     Maps maps;
     memset(&maps, 0, sizeof(maps));
     const Cfg cf = cfg_for(mode);
@@ -577,7 +584,7 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         const Plane &pa = aplanes[i < na ? i : 0];
         const Plane &pb = bplanes[i < nb ? i : 0];
         if (!encode_plane(&maps.a[i], pa, 64, cf.ks)) return cudaErrorInvalidValue;
-        if (!encode_plane(&maps.b[i], pb, cf.ks, BN, cf.ks == 32)) return cudaErrorInvalidValue;
+        if (!encode_plane(&maps.b[i], pb, cf.ks, bn, cf.ks == 32)) return cudaErrorInvalidValue;
     }
     // Stage layout: every distinct plane the terms read (fused), or one term's pair.
     Pipe pipe{1, 1, 0, 0, 0};
@@ -588,7 +595,7 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
             pipe.nb = std::max(pipe.nb, terms.b[j] + 1);
         }
     }
-    pipe.stage_bytes = (pipe.na * BM + pipe.nb * BN) * cf.ks * 2;
+    pipe.stage_bytes = (pipe.na * BM + pipe.nb * bn) * cf.ks * 2;
     pipe.batched = aplanes[0].batch > 1 ? 1 : 0;
     for (int i = 0; i < na; ++i)
         if ((aplanes[i].batch > 1) != (pipe.batched != 0)) return cudaErrorInvalidValue;
@@ -596,25 +603,36 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         if ((bplanes[i].batch > 1) != (pipe.batched != 0)) return cudaErrorInvalidValue;
     pipe.stages = std::min(MAX_STAGES, STAGE_BUDGET / pipe.stage_bytes);
     TraceScope ts(c.stream, trace_name, flops, 0.0);
-#define TRI_TC_CASE(M)                                                                   \
-    case M:                                                                              \
-        if (trans) return unit ? launch_t<M, true, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)   \
-                               : launch_t<M, true, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi); \
-        return unit ? launch_t<M, false, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)             \
-                    : launch_t<M, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+#define TRI_TC_CASE_N(M, N)                                                                   \
+        if (trans) return unit ? launch_t<M, true, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)   \
+                               : launch_t<M, true, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi); \
+        return unit ? launch_t<M, false, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)             \
+                    : launch_t<M, false, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+#define TRI_TC_CASE(M) \
+    case M:            \
+        TRI_TC_CASE_N(M, BN)
+#define TRI_TC_CASE_LEVEL(M)                 \
+    case M:                                  \
+        if (bn == 64) { TRI_TC_CASE_N(M, 64) } \
+        if (bn == 128) { TRI_TC_CASE_N(M, 128) } \
+        TRI_TC_CASE_N(M, BN)
     switch (mode) {
-        TRI_TC_CASE(MODE_W)
-        TRI_TC_CASE(MODE_X21)
+        TRI_TC_CASE_LEVEL(MODE_W)
+        TRI_TC_CASE_LEVEL(MODE_X21)
         TRI_TC_CASE(MODE_RES)
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:
             return launch_t<MODE_F32, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
         case MODE_GEN:
             return launch_t<MODE_GEN, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+        case MODE_GENP:
+            return launch_t<MODE_GENP, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
         default:
             return cudaErrorInvalidValue;
     }
 #undef TRI_TC_CASE
+#undef TRI_TC_CASE_LEVEL
+#undef TRI_TC_CASE_N
 }
 
 }  // namespace tc
@@ -650,7 +668,7 @@ extern "C" tri_status tri_tc_gemm_bf16(int64_t m, int64_t n, int64_t k, int nter
     const int ctas = tc::schedule_lpt(v, nterms, ctx.sm_count, off);
     const size_t tbytes = v.size() * sizeof(tc::Tile), obytes = off.size() * sizeof(int);
     uint8_t *d = nullptr;
-    if (cudaMallocAsync((void **)&d, tbytes + obytes, ctx.stream) != cudaSuccess) {
+    if (lib_malloc_async((void **)&d, tbytes + obytes, ctx.stream) != cudaSuccess) {
         cudaGetLastError();
         return TRI_ERR_NOMEM;
     }

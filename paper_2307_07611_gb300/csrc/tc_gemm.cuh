@@ -40,6 +40,7 @@ struct Epi {
     float alpha = 1.f, beta = 0.f; // MODE_GEN: x <- alpha * acc + beta * x
     int cmask = 0;                 // MODE_GEN: part of x written: 0 full, 1 lower, 2 upper,
                                    // 3 / 4 strict lower / upper with a zero diagonal
+    float dadd = 0.f;              // MODE_GEN (cmask 0..2): added to diagonal entries
     int64_t xs = 0, os = 0;        // batch strides (elements) of x and of the output planes
 };
 
@@ -50,6 +51,8 @@ enum Mode {
     MODE_UPD = 3,    // x += acc on the lower triangle                       (X += X R)
     MODE_F32 = 4,    // x <- acc (plain column-major store, no view)        (verification)
     MODE_GEN = 5,    // x <- alpha acc + beta x, column-major, masked        (general products)
+    MODE_GENP = 6,   // MODE_GEN with fused stages and FP32 promotion of the partial sums
+                     // every 64 k (the six-term products that must reach ~2^-24)
 };
 
 // A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld
@@ -76,10 +79,12 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
 // Encodes the tensor maps, then launches `ctas` persistent CTAs; CTA b processes the
 // tiles d_tiles[d_off[b] .. d_off[b+1]).  aplanes/bplanes: up to 3 planes each, indexed
 // by `terms`.
+// bn: columns of the output tiles the list was built with: BN, or 128 / 64 for the level
+// products (MODE_W, MODE_X21).
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
                       int na, const Plane *bplanes, int nb, const Terms &terms,
                       const Tile *d_tiles, const int *d_off, int ctas, const Epi &epi,
-                      double flops, const char *trace_name);
+                      double flops, const char *trace_name, int bn = BN);
 
 }  // namespace tc
 }  // namespace triinv

@@ -42,7 +42,7 @@ def _declare(lib):
         "tri_version": ([], ctypes.c_char_p),
         "tri_inv": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "tri_inv_workspace_size": ([i64, i32], sz),
-        "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp], i32),
+        "tri_inv_ex": ([i32, i32, i64, vp, i64, i32, vp, sz, vp, vp], i32),
         "tri_get_info": ([vp, ctypes.POINTER(i64)], i32),
         "tri_inv_noalloc": ([i32, i32, i64, vp, i64, i32, vp], i32),
         "tri_inv_host": ([i32, i32, i64, vp, i64, i32, vp, ctypes.POINTER(i64)], i32),
@@ -50,7 +50,7 @@ def _declare(lib):
         "gen_inv": ([i64, vp, i64, i32, vp], i32),
         "tri_inv_strided_batched": ([i32, i32, i64, vp, i64, i64, i64, i32, vp], i32),
         "tri_inv_strided_batched_workspace_size": ([i64, i64, i32], sz),
-        "tri_inv_strided_batched_ex": ([i32, i32, i64, vp, i64, i64, i64, i32, vp, sz, vp], i32),
+        "tri_inv_strided_batched_ex": ([i32, i32, i64, vp, i64, i64, i64, i32, vp, sz, vp, vp], i32),
         "tri_inv_backward": ([i32, i32, i64, vp, i64, vp, i64, vp, i64, i32, vp], i32),
         "tri_inv_backward_strided_batched": ([i32, i32, i64, vp, i64, i64, vp, i64, i64, vp, i64, i64, i64,
                                               i32, vp], i32),
@@ -65,17 +65,21 @@ def _declare(lib):
         "tri_batched_plan_set_growth_limit": ([vp, ctypes.c_double], i32),
         "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
-        "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp], i32),
+        "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp, vp], i32),
         "skul": ([i64, vp, i64, vp, i64, i32, vp], i32),
         "skul_workspace_size": ([i64, i32], sz),
-        "skul_ex": ([i64, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+        "skul_ex": ([i64, vp, i64, vp, i64, i32, vp, sz, vp, vp], i32),
         "sqr": ([i64, vp, i64, vp, i64, vp, i64, i32, vp], i32),
         "sqr_workspace_size": ([i64, i32], sz),
-        "sqr_ex": ([i64, vp, i64, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+        "sqr_ex": ([i64, vp, i64, vp, i64, vp, i64, i32, vp, sz, vp, vp], i32),
         "sqr_inv": ([i64, vp, i64, i32, vp], i32),
         "tri_tc_gemm_bf16": ([i64, i64, i64, i32, ctypes.POINTER(vp), i64, ctypes.POINTER(vp), i64,
                               vp, i64, vp], i32),
         "tri_mixed_schedule_stats": ([i64, i32, ctypes.POINTER(ctypes.c_double), i32], i32),
+        "tri_batched_partition": ([i64, ctypes.POINTER(i64), i32, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_double)], i32),
+        "tri_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "tri_pool_stats": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), i32], i32),
         "tri_trace_enable": ([i32], None),
         "tri_trace_report": ([ctypes.c_char_p, sz], i64),
         "tri_trace_timeline": ([ctypes.POINTER(ctypes.c_uint64), sz], i64),
@@ -122,8 +126,10 @@ def tri_inv_workspace_size(n, dtype) -> int:
     return int(load().tri_inv_workspace_size(n, dtype))
 
 
-def tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
-    return load().tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace or None, ws_bytes,
+def tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace, ws_bytes, stream=0, d_info=0) -> int:
+    """d_info: 0 (pivots to the device-wide word of tri_get_info) or the device address of
+    an int64 that receives the first bad pivot index or -1 (the C argument before stream)."""
+    return load().tri_inv_ex(uplo, diag, n, ptr, ld, dtype, workspace or None, ws_bytes, d_info or None,
                              stream or None)
 
 
@@ -135,8 +141,8 @@ def gen_inv_workspace_size(n, dtype) -> int:
     return int(load().gen_inv_workspace_size(n, dtype))
 
 
-def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0) -> int:
-    return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, stream or None)
+def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0, d_info=0) -> int:
+    return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, d_info or None, stream or None)
 
 
 def skul(n, a_ptr, lda, sk_ptr, ldsk, dtype, stream=0) -> int:
@@ -147,8 +153,9 @@ def skul_workspace_size(n, dtype) -> int:
     return int(load().skul_workspace_size(n, dtype))
 
 
-def skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace, ws_bytes, stream=0) -> int:
-    return load().skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace or None, ws_bytes, stream or None)
+def skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace, ws_bytes, stream=0, d_info=0) -> int:
+    return load().skul_ex(n, a_ptr, lda, sk_ptr, ldsk, dtype, workspace or None, ws_bytes, d_info or None,
+                          stream or None)
 
 
 def sqr(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, stream=0) -> int:
@@ -159,9 +166,9 @@ def sqr_workspace_size(n, dtype) -> int:
     return int(load().sqr_workspace_size(n, dtype))
 
 
-def sqr_ex(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, workspace, ws_bytes, stream=0) -> int:
+def sqr_ex(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, workspace, ws_bytes, stream=0, d_info=0) -> int:
     return load().sqr_ex(n, a_ptr, lda, r_ptr, ldr, s_ptr, lds, dtype, workspace or None, ws_bytes,
-                         stream or None)
+                         d_info or None, stream or None)
 
 
 def sqr_inv(n, a_ptr, lda, dtype, stream=0) -> int:
@@ -202,6 +209,17 @@ def tri_inv_batched(count, sizes, ptrs, uplo, diag, dtype, stream=0) -> int:
     return load().tri_inv_batched(count, sz, pt, uplo, diag, dtype, stream or None)
 
 
+def tri_batched_partition(sizes, world):
+    """(owner, loads): the rank of every block (longest first to the least-loaded rank by
+    m^3) and each rank's sum of m^3 -- the multi-GPU split of a batch (no collective)."""
+    n = len(sizes)
+    sz = (ctypes.c_int64 * max(n, 1))(*[int(k) for k in sizes])
+    own = (ctypes.c_int32 * max(n, 1))()
+    loads = (ctypes.c_double * max(int(world), 1))()
+    check(load().tri_batched_partition(n, sz, int(world), own, loads), "tri_batched_partition")
+    return [int(own[i]) for i in range(n)], [float(loads[r]) for r in range(int(world))]
+
+
 def tri_inv_strided_batched(uplo, diag, n, ptr, ld, stride, batch, dtype, stream=0) -> int:
     return load().tri_inv_strided_batched(uplo, diag, n, ptr, ld, stride, batch, dtype, stream or None)
 
@@ -210,9 +228,10 @@ def tri_inv_strided_batched_workspace_size(n, batch, dtype) -> int:
     return int(load().tri_inv_strided_batched_workspace_size(n, batch, dtype))
 
 
-def tri_inv_strided_batched_ex(uplo, diag, n, ptr, ld, stride, batch, dtype, workspace, ws_bytes, stream=0) -> int:
+def tri_inv_strided_batched_ex(uplo, diag, n, ptr, ld, stride, batch, dtype, workspace, ws_bytes, stream=0,
+                               d_info=0) -> int:
     return load().tri_inv_strided_batched_ex(uplo, diag, n, ptr, ld, stride, batch, dtype, workspace or None,
-                                             ws_bytes, stream or None)
+                                             ws_bytes, d_info or None, stream or None)
 
 
 def tri_inv_backward(uplo, diag, n, x, ldx, g, ldg, dt, lddt, dtype, stream=0) -> int:
@@ -283,6 +302,20 @@ def tri_get_info(stream=0):
     idx = ctypes.c_int64(-1)
     st = load().tri_get_info(stream or None, ctypes.byref(idx))
     return st, idx.value
+
+
+def tri_alu_peak(dtype, iters: int = 1 << 16):
+    """(TFLOP/s, ms): measured FFMA (TRI_F32) or DFMA (TRI_F64) peak of the current device."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(load().tri_alu_peak(int(dtype), int(iters), ctypes.byref(tf), ctypes.byref(ms)), "tri_alu_peak")
+    return float(tf.value), float(ms.value)
+
+
+def tri_pool_stats(reset_high: bool = False):
+    """(used, used_high) bytes of the library's scratch pool on the current device."""
+    used, high = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(load().tri_pool_stats(ctypes.byref(used), ctypes.byref(high), 1 if reset_high else 0), "tri_pool_stats")
+    return int(used.value), int(high.value)
 
 
 def tri_trace_enable(on: bool):

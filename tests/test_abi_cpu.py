@@ -74,6 +74,18 @@ def test_workspace_checks_need_no_gpu(libtri):
     assert lib.tri_inv_workspace_size(64, lib.TRI_F32) == 0   # a single leaf
 
 
+def test_noalloc_limits_fit_its_scratch(libtri):
+    """The documented limits of tri_inv_noalloc (FP32 n <= 4096, FP64 n <= 2048) follow from
+    tri_inv_workspace_size and the array size declared in the header."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "triinv.h")).read()
+    m = re.search(r"#define TRI_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", hdr)
+    cap = int(m.group(1)) << int(m.group(2))
+    assert cap == lib.TRI_NOALLOC_SCRATCH_BYTES
+    assert lib.tri_inv_workspace_size(4096, lib.TRI_F32) <= cap < lib.tri_inv_workspace_size(4097, lib.TRI_F32)
+    assert lib.tri_inv_workspace_size(2048, lib.TRI_F64) <= cap < lib.tri_inv_workspace_size(2049, lib.TRI_F64)
+
+
 def test_plain_workspace_formula(libtri):
     # one h x h block per active pair at the widest level, leaf 64
     for n, es, dt in [(8192, 4, lib.TRI_F32), (512, 8, lib.TRI_F64), (1000, 4, lib.TRI_F32)]:

@@ -2,9 +2,9 @@
 S = U^-1 formed alongside) against the FP64 oracle, which runs the algorithm as printed.
 
 Each factor F in {L, U, S, K} is compared as max |F - F_oracle| / max |F_oracle| with the
-tolerances of gen_inv (the same block recursion): FP64 / FP32 40 sqrt(n) u, mixed
-(three-term split-BF16 products) 0.25 sqrt(n) 2^-16.  Independently of the oracle:
-||L U - A||_F / ||A||_F and the normwise residual of S K as an inverse.
+tolerances of gen_inv (the same block recursion): 40 sqrt(n) u for FP64, FP32 and mixed
+(six-term split-BF16 products with FP32 promotion, u = 2^-24).  Independently of the
+oracle: ||L U - A||_F / ||A||_F and the normwise residual of S K as an inverse.
 """
 import numpy as np
 import pytest
@@ -33,9 +33,7 @@ def code_of(lib, dt):
 
 
 def tol(n, dt):
-    if dt == "mixed":
-        return 0.25 * np.sqrt(n) * 2.0 ** -16
-    return 40.0 * np.sqrt(max(n, 1)) * U[dt]
+    return 40.0 * np.sqrt(max(n, 1)) * U["f64" if dt == "f64" else "f32"]
 
 
 def run_skul(lib, a, dt, pad_a=3, pad_sk=5, workspace=False):

@@ -157,15 +157,13 @@ def test_torch_helper_rowmajor(lib):
 @pytest.mark.slow
 @pytest.mark.parametrize("lower", [True, False])
 def test_full_size_f32_n8192_sampled(lib, lower):
-    """The FP32 n = 8192 workload (normal law): sampled columns of the lower view
-    against the oracle and the normwise residual of the whole result."""
+    """The FP32 n = 8192 workload (normal law): every element against the FP64 oracle
+    (all 8192 columns) and the normwise residual of the whole result."""
     n = 8192
     t = inputs.tri_lower(n, seed=0, law="normal", dtype=np.float32).astype(np.float64)
     tt = t if lower else t.T.copy()
     x, st = run_tri_inv(lib, torch, tt, lower=lower, dtype="f32", ld_pad=0)
     assert st == lib.TRI_OK
-    cols = [0, 1, 63, 64, 4095, 4096, 5000, 8190, 8191]
-    want = oracle.tri_inv_cols(tt, cols, lower=lower)
-    got = x[:, cols] if lower else x[cols, :].T
-    assert rel_max_err(got, want) <= tol(n, "f32")
+    want = oracle.tri_inv(tt, lower=lower)
+    assert rel_max_err(x, want) <= tol(n, "f32")
     assert normwise_residual(tt, x) <= 5e-6

@@ -406,3 +406,30 @@ def test_tri_grad_ignores_other_triangle_of_g():
     g2 = g.copy()
     g2[np.triu_indices(n, 1)] = 1e3
     assert np.abs(oracle.tri_grad(x, g) - oracle.tri_grad(x, g2)).max() < 1e-9
+
+
+def test_prepared_view_gives_the_same_columns():
+    """oracle.LowerView only shares the preparation of the lower view between requests:
+    its columns are bit-identical to tri_inv_cols (lower, upper and unit views)."""
+    t = inputs.tri_lower(97, seed=3, law="normal")
+    cols = [0, 1, 40, 96]
+    for lower, unit in ((True, False), (False, False), (True, True)):
+        m = t if lower else t.T.copy()
+        a = oracle.LowerView(m, lower=lower, unit=unit).cols(cols)
+        b = oracle.tri_inv_cols(m, cols, lower=lower, unit=unit)
+        assert np.array_equal(a, b)
+
+
+def test_inverse_columns_match_gen_inv_and_solve_the_system():
+    """oracle.inverse_columns (A x = e_j by a library solve) agrees with the pinned
+    oracle.gen_inv (Crout, U^-1 L^-1, Section 5.1) and solves A x = e_j to FP64 rounding."""
+    n = 300
+    a = inputs.general(n, seed=9, dtype=np.float64)
+    cols = [0, 7, 150, 299]
+    x = oracle.inverse_columns(a, cols)
+    full = oracle.gen_inv(a)
+    assert np.abs(x - full[:, cols]).max() <= 1e-12 * np.abs(full).max()
+    e = np.zeros((n, len(cols)))
+    e[cols, range(len(cols))] = 1.0
+    assert np.abs(a @ x - e).max() <= 1e-13
+
