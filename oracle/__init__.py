@@ -9,6 +9,9 @@ Two layers:
 * ``oracle.c`` (compiled here with gcc): the column recurrence of CRIT (Section 4.2),
   Crout LU in SKUL's row order (Section 5.1), A^-1 = U^-1 L^-1, Algorithms SKUL and SQR
   as printed (Section 5.1) and the adjoint dT = -P(X^T G X^T).  Plain loops in binary64, no fast-math, no FMA contraction.
+* NumPy pieces (matrix products as a library primitive): BRSI with gamma blocks
+  (Section 5.2, the steps of BRSI(gamma): A_{l+1} = I + M_l^-1 N_l, A = M_0 ... L,
+  Step 1's column permutation P_0), and columns of A^-1 by a library solve.
 * Pure-Python pieces for tiny sizes: the Hopscotch series H(a, b) (Definition 3.1,
   Example "H(1,5)"), the combinatorial entry formula of the main Theorem of Section 3
   (Eq. "TMatrixInversecombinatorixFormula") and an instrumented CRIT* that counts its
@@ -217,6 +220,116 @@ def gen_inv(a, threads: int = 0) -> np.ndarray:
     if n:
         _check(_load().oracle_gen_inv(n, ac.ctypes.data, n, x.ctypes.data, n, threads))
     return np.ascontiguousarray(x)
+
+
+# --- BRSI with gamma blocks (Section 5.2, "Steps of BRSI(gamma)") ----------------------
+
+def brsi_bounds(n: int, gamma: int):
+    """Block boundaries of the gamma-block split: blocks of q = ceil(n / gamma) rows, the
+    last one ragged; empty blocks are dropped (so n < gamma gives n blocks of one)."""
+    q = -(-n // gamma) if n else 1
+    b = sorted(set(min(i * q, n) for i in range(gamma + 1)))
+    return b
+
+
+def _block_upper_inverse(m, b, gamma, leaf):
+    """Inverse of the block upper triangular M (diagonal blocks full) by block back
+    substitution: X_ii = M_ii^-1 (by BRSI itself, the double recursion of Step 4), then
+    for j > i, X_ij = -X_ii sum_{k=i+1}^{j} M_ik X_kj."""
+    nb = len(b) - 1
+    x = np.zeros_like(m)
+    for i in range(nb):
+        s = slice(b[i], b[i + 1])
+        x[s, s] = _brsi_core(m[s, s], gamma, leaf)
+    for j in range(nb):
+        sj = slice(b[j], b[j + 1])
+        for i in range(j - 1, -1, -1):
+            si = slice(b[i], b[i + 1])
+            acc = np.zeros((b[i + 1] - b[i], b[j + 1] - b[j]))
+            for k in range(i + 1, j + 1):
+                sk = slice(b[k], b[k + 1])
+                acc += m[si, sk] @ x[sk, sj]
+            x[si, sj] = -(x[si, si] @ acc)
+    return x
+
+
+def _block_lower_inverse(l_, b, gamma, leaf):
+    """Inverse of the block lower triangular L (diagonal blocks full) by block forward
+    substitution: X_ii = L_ii^-1, then for i > j, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj."""
+    nb = len(b) - 1
+    x = np.zeros_like(l_)
+    for i in range(nb):
+        s = slice(b[i], b[i + 1])
+        x[s, s] = _brsi_core(l_[s, s], gamma, leaf)
+    for j in range(nb):
+        sj = slice(b[j], b[j + 1])
+        for i in range(j + 1, nb):
+            si = slice(b[i], b[i + 1])
+            acc = np.zeros((b[i + 1] - b[i], b[j + 1] - b[j]))
+            for k in range(j, i):
+                sk = slice(b[k], b[k + 1])
+                acc += l_[si, sk] @ x[sk, sj]
+            x[si, sj] = -(x[si, si] @ acc)
+    return x
+
+
+def brsi_factors(a, gamma: int, leaf: int = 8):
+    """The factors of Steps 2-5 of BRSI(gamma) (Section 5.2) for A (no permutation):
+    returns (b, [M_0, ..., M_{nb-2}], [M_0^-1, ...], L) with A = M_0 M_1 ... M_{nb-2} L.
+
+    For l = 0 .. nb - 2 (nb blocks of the split, boundaries b):
+        A_l = M_l + N_l   (M_l: the block upper part of A_l, diagonal blocks included;
+                           N_l: its strictly block lower part)
+        A_{l+1} = I + M_l^-1 N_l
+    N_l has a zero last block column, and so on: A_{l+1} has l + 1 trailing block columns
+    that are identity columns above and on the diagonal, and M_{l+1} is the identity
+    there.  After the loop L = A_{nb-1} is block lower triangular (one full diagonal
+    block, the others the identity).  Diagonal blocks of the M_l are inverted by BRSI
+    itself (the double recursion of Step 4)."""
+    n = a.shape[0]
+    b = brsi_bounds(n, gamma)
+    nb = len(b) - 1
+    al = np.array(a, dtype=np.float64, copy=True)
+    ms, minvs = [], []
+    for _ in range(nb - 1):
+        m = np.zeros((n, n))
+        for i in range(nb):
+            for j in range(i, nb):
+                m[b[i]:b[i + 1], b[j]:b[j + 1]] = al[b[i]:b[i + 1], b[j]:b[j + 1]]
+        nmat = al - m
+        minv = _block_upper_inverse(m, b, gamma, leaf)
+        al = np.eye(n) + minv @ nmat
+        ms.append(m)
+        minvs.append(minv)
+    return b, ms, minvs, al
+
+
+def _brsi_core(a, gamma, leaf):
+    """A^-1 = L^-1 M_{nb-2}^-1 ... M_0^-1 from brsi_factors.  Blocks of at most `leaf`
+    rows are inverted directly by the Crout route of gen_inv (Section 5.1)."""
+    n = a.shape[0]
+    if n <= leaf:
+        return gen_inv(a)
+    b, _, minvs, l_ = brsi_factors(a, gamma, leaf)
+    y = np.eye(n)
+    for minv in minvs:
+        y = minv @ y
+    return _block_lower_inverse(l_, b, gamma, leaf) @ y
+
+
+def brsi(a, gamma: int, perm=None, leaf: int = 8) -> np.ndarray:
+    """A^-1 by BRSI(gamma) (Section 5.2) in FP64.  perm: the column permutation P_0 of
+    Step 1 (A_0 = A P_0, column j of A_0 is column perm[j] of A; None = identity); the
+    later permutations P_l are the identity.  Then A^-1 = P_0 (A P_0)^-1: row perm[j] of
+    A^-1 is row j of (A P_0)^-1.  The block products are matrix products (a library
+    primitive); nothing else is blocked or reordered beyond the paper's steps."""
+    a = np.asarray(a, dtype=np.float64)
+    n = a.shape[0]
+    p = np.arange(n) if perm is None else np.asarray(perm, dtype=np.int64)
+    x = _brsi_core(a[:, p], int(gamma), int(leaf))
+    out = np.empty_like(x)
+    out[p, :] = x
+    return out
 
 
 def tri_grad(x, g, lower: bool = True, unit: bool = False, threads: int = 0) -> np.ndarray:

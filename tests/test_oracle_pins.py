@@ -433,3 +433,82 @@ def test_inverse_columns_match_gen_inv_and_solve_the_system():
     e[cols, range(len(cols))] = 1.0
     assert np.abs(a @ x - e).max() <= 1e-13
 
+
+
+# --- Section 5.2: BRSI with gamma blocks ----------------------------------------------
+
+def _gamma2_closed_form(a, m1):
+    """The last block formula of Section 5.2 for gamma = 2 (Schur complement form):
+    A^-1 = [Z, -Z A12 A22^-1; -A22^-1 A21 Z, A22^-1 A21 Z A12 A22^-1 + A22^-1] with
+    Z = (A11 - A12 A22^-1 A21)^-1, computed with LAPACK inverses."""
+    a11, a12, a21, a22 = a[:m1, :m1], a[:m1, m1:], a[m1:, :m1], a[m1:, m1:]
+    i22 = np.linalg.inv(a22)
+    z = np.linalg.inv(a11 - a12 @ i22 @ a21)
+    return np.block([[z, -z @ a12 @ i22], [-i22 @ a21 @ z, i22 @ a21 @ z @ a12 @ i22 + i22]])
+
+
+@pytest.mark.parametrize("n", [6, 40, 129])
+def test_brsi_gamma2_matches_the_printed_block_formula(n):
+    a = inputs.general(n, seed=n, dtype=np.float64)
+    m1 = oracle.brsi_bounds(n, 2)[1]
+    want = _gamma2_closed_form(a, m1)
+    assert np.abs(oracle.brsi(a, 2, leaf=4) - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("n,gamma", [(7, 3), (50, 3), (64, 4), (97, 5), (200, 8), (16, 16)])
+def test_brsi_equals_the_inverse(n, gamma):
+    a = inputs.general(n, seed=n + gamma, dtype=np.float64)
+    x = oracle.brsi(a, gamma, leaf=4)
+    want = np.linalg.inv(a)
+    assert np.abs(x - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(a @ x - np.eye(n)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("gamma", [2, 3, 4])
+def test_brsi_factorisation_structure(gamma):
+    """A = M_0 M_1 ... M_{nb-2} L (Section 5.2, "A P = U_0 U_1 ... L"): every M_l block
+    upper triangular with identity blocks where the earlier steps made the columns
+    canonical, L block lower triangular with identity diagonal blocks after the first."""
+    n = 45
+    a = inputs.general(n, seed=3, dtype=np.float64)
+    b, ms, minvs, l_ = oracle.brsi_factors(a, gamma, leaf=4)
+    nb = len(b) - 1
+    prod = np.eye(n)
+    for m in ms:
+        prod = prod @ m
+    assert np.abs(prod @ l_ - a).max() <= 1e-12
+    for li, (m, mi) in enumerate(zip(ms, minvs)):
+        assert np.abs(m @ mi - np.eye(n)).max() <= 1e-12
+        for i in range(nb):
+            for j in range(nb):
+                blk = m[b[i]:b[i + 1], b[j]:b[j + 1]]
+                if j < i:
+                    assert not blk.any()                          # block upper
+                if j >= nb - li and i == j:
+                    assert np.array_equal(blk, np.eye(blk.shape[0]))   # canonical columns
+    for i in range(nb):
+        for j in range(nb):
+            blk = l_[b[i]:b[i + 1], b[j]:b[j + 1]]
+            if j > i:
+                assert not blk.any()                              # block lower
+            if i == j and i > 0:
+                assert np.array_equal(blk, np.eye(blk.shape[0]))
+
+
+def test_brsi_paper_example_and_permutation():
+    """The 5x5 example of Section 6.1 (printed inverse factors S K), for gamma = 2..5; and
+    Step 1's column permutation P_0: a matrix whose diagonal blocks are singular is
+    inverted once P_0 swaps its block columns, and A^-1 = P_0 (A P_0)^-1."""
+    g = matrices("skul_sqr_5x5.txt")
+    for gamma in (2, 3, 4, 5):
+        assert np.abs(oracle.brsi(g["A"], gamma, leaf=1) - g["S"] @ g["K"]).max() < 2e-4
+    n = 40
+    rng = np.random.default_rng(5)
+    a = np.zeros((n, n))
+    a[:20, 20:] = np.eye(20) * 2.0 + rng.standard_normal((20, 20)) / np.sqrt(n)
+    a[20:, :20] = np.eye(20) * 2.0 + rng.standard_normal((20, 20)) / np.sqrt(n)
+    perm = np.r_[np.arange(20, 40), np.arange(0, 20)]
+    x = oracle.brsi(a, 2, perm=perm, leaf=4)
+    assert np.abs(x - np.linalg.inv(a)).max() <= 1e-12 * np.abs(x).max()
+    with pytest.raises(oracle.SingularError):
+        oracle.brsi(a, 2, leaf=4)                                 # A_11 = 0 without P_0
