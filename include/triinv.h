@@ -144,6 +144,37 @@ TRI_API tri_status gen_inv_ex(int64_t n, void *a, int64_t lda, tri_dtype dtype, 
                               size_t ws_bytes, int64_t *d_info, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * BRSI with gamma blocks (Section 5.2, "Steps of BRSI(gamma)"), in place: A <- A^-1.
+ * Step 1: A_0 = A P_0 with the caller's column permutation P_0.  Steps 2-5, gamma - 1
+ * times: A_l = M_l + N_l (M_l the block upper part of A_l, diagonal blocks included; N_l
+ * the strictly block lower part), A_{l+1} = I + M_l^-1 N_l.  Then A P_0 = M_0 ... M_{g-2} L
+ * with L = A_{g-1} block lower triangular, and A^-1 = P_0 L^-1 M_{g-2}^-1 ... M_0^-1.  The
+ * diagonal blocks of the M_l and L are inverted by gen_inv (the two-block form: the
+ * double recursion of Step 4); the rest are block products.  The work grows with gamma.
+ *   n      order, 0 <= n <= 65535;  a: device, lda x n column-major, lda >= max(1, n).
+ *   gamma  number of blocks, 2..16 (blocks of ceil(n / gamma) rows, the last ragged).
+ *   perm   HOST array of n distinct indices (column j of A P_0 is column perm[j] of A), or
+ *          NULL for the identity.  The later permutations P_l of the paper ("as necessary")
+ *          are the identity: choose P_0 so that the diagonal blocks of every A_l are
+ *          non-singular (e.g. block columns swapped when a diagonal block of A is
+ *          singular).  With perm the call copies it from host memory (do not capture).
+ *   dtype  TRI_F64 / TRI_F32 (CUDA-core products) or TRI_F32_MIXED (three-term split-BF16
+ *          tensor-core products, then one Newton-Schulz step against A for n >= 512).
+ * A zero or non-finite pivot in a diagonal-block inverse is reported by tri_get_info (or
+ * d_info) as the row of A_l where that block's pivot lies; the result is then unspecified.
+ * Errors: TRI_ERR_ARG (bad dtype, n < 0, gamma outside 2..16, null a, small lda, perm not
+ * a permutation), TRI_ERR_UNSUPPORTED (n > 65535), TRI_ERR_NOMEM, TRI_ERR_CUDA.
+ * --------------------------------------------------------------------------------- */
+TRI_API tri_status brsi_inv(int64_t n, void *a, int64_t lda, int gamma, const int64_t *perm, tri_dtype dtype,
+                            void *stream);
+/* Bytes of 256-byte aligned device scratch brsi_inv_ex needs (4 n^2 elements, the gen_inv
+ * scratch of one diagonal block, the BF16 planes of an n x n product for mixed). */
+TRI_API size_t brsi_inv_workspace_size(int64_t n, int gamma, tri_dtype dtype);
+/* brsi_inv with caller scratch and an optional per-call status word (as tri_inv_ex). */
+TRI_API tri_status brsi_inv_ex(int64_t n, void *a, int64_t lda, int gamma, const int64_t *perm, tri_dtype dtype,
+                               void *workspace, size_t ws_bytes, int64_t *d_info, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * SKUL (Algorithm SKUL, Section 5.1): the unpivoted Crout factorisation A = L U together
  * with the inverse factors K = L^-1 and S = U^-1, so that A^-1 = S K, for preconditioners
  * that want the direct and the inverse factors at once.  Computed block-recursively as in
@@ -409,6 +440,21 @@ TRI_API tri_status tri_mixed_schedule_stats(int64_t n, int ctas, double *stats, 
  * out, otherwise TRI_OK with *first_bad_index = -1.  first_bad_index is a host pointer
  * and may be NULL. */
 TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
+
+/* Growth limit of the FP64 fallback for ill-conditioned diagonal blocks on the
+ * single-matrix paths (tri_inv, tri_inv_ex, the strided batches; FP32 and mixed), process-
+ * wide, default 1e4 (the paper is silent on ill-conditioned leaves).  After a diagonal
+ * block's FP32 inverse -- a plain-path leaf of 64 rows, or a mixed-path diagonal block of
+ * 256 rows -- the growth max|X| max|T| (a lower bound of the block's condition number in
+ * the max norm) is compared with tau; above it the block, still unchanged in memory, is
+ * inverted again with FP64 arithmetic and that result, rounded to FP32, is kept.  On the
+ * mixed path a matrix with such a block also skips the Newton-Schulz step: its residual,
+ * computed to FP32 accuracy, would be dominated by rounding once max|X| max|T| is large.
+ * tau <= 0 disables the check (results then bit-identical to a run without it on every
+ * input); tri_growth_limit returns the current value.
+ * Errors: TRI_ERR_ARG (NaN). */
+TRI_API tri_status tri_set_growth_limit(double tau);
+TRI_API double tri_growth_limit(void);
 
 /* Measured CUDA-core peak of the current device for dtype TRI_F32 (FFMA) or TRI_F64
  * (DFMA), in TFLOP/s (2 flops per fused multiply-add): every thread of a full grid runs 8

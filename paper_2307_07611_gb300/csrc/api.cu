@@ -11,6 +11,7 @@
 //   level 0: every leaf block is inverted by the CRIT column recurrence (leaf.cu);
 //   level s: for every pair, W = B X_A then B <- -X_C W (trmm_simt.cu / tc_gemm.cu).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,11 @@ struct DeviceState {
 std::mutex g_mu;
 DeviceState g_dev[64];
 
+// Growth limit of the FP64 fallback on the single-matrix paths (plain leaves, the mixed
+// path's diagonal blocks): max|X| max|T| of a diagonal block's FP32 inverse above it
+// triggers an FP64 inverse of that block.  Process-wide; <= 0 disables.
+std::atomic<float> g_growth_tau{1.0e4f};
+
 tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TRI_ERR_CUDA;
@@ -60,6 +66,7 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     out->timeout = d.timeout;
     out->sm_count = d.sm_count;
     out->device = dev;
+    out->tau = g_growth_tau.load(std::memory_order_relaxed);
     return TRI_OK;
 }
 
@@ -232,8 +239,12 @@ size_t combrit_ws_bytes(int64_t n, tri_dtype dt, int beta);
 tri_status run_combrit(const Ctx &c, tri_dtype dt, bool trans, bool unit, int64_t n, void *a, int64_t lda, int beta,
                        void *ws);
 size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt);
-tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws);
+tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws,
+                       int64_t info_base = 0);
 size_t skul_ws_bytes(int64_t n, tri_dtype dt);
+size_t brsi_ws_bytes(int64_t n, int gamma, tri_dtype dt);
+tri_status run_brsi(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, int gamma, const int64_t *perm,
+                    void *ws);
 tri_status run_skul(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *sk, int64_t ldsk, void *ws);
 size_t sqr_ws_bytes(int64_t n, tri_dtype dt);
 tri_status run_sqr(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *r, int64_t ldr, void *s,
@@ -422,6 +433,58 @@ tri_status gen_inv(int64_t n, void *a, int64_t lda, tri_dtype dtype, void *strea
     return st;
 }
 
+size_t brsi_inv_workspace_size(int64_t n, int gamma, tri_dtype dtype) {
+    if (n <= 0 || gamma < 2 || gamma > 16 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
+    return brsi_ws_bytes(n, gamma, dtype);
+}
+
+static bool valid_perm(int64_t n, const int64_t *perm) {
+    if (!perm) return true;
+    std::vector<char> seen((size_t)n, 0);
+    for (int64_t j = 0; j < n; ++j) {
+        if (perm[j] < 0 || perm[j] >= n || seen[(size_t)perm[j]]) return false;
+        seen[(size_t)perm[j]] = 1;
+    }
+    return true;
+}
+
+tri_status brsi_inv_ex(int64_t n, void *a, int64_t lda, int gamma, const int64_t *perm, tri_dtype dtype,
+                       void *workspace, size_t ws_bytes, int64_t *d_info, void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0 || gamma < 2 || gamma > 16) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n) || !valid_perm(n, perm)) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    const size_t need = brsi_ws_bytes(n, gamma, dtype);
+    if (ws_bytes < need || !workspace || ((uintptr_t)workspace & 255)) return TRI_ERR_NOMEM;
+    Ctx c;
+    tri_status st = device_ctx((cudaStream_t)stream, &c);
+    if (st != TRI_OK) return st;
+    if ((st = info_begin(c, d_info)) != TRI_OK) return st;
+    return info_end(c, d_info, run_brsi(c, dtype, n, a, lda, gamma, perm, workspace));
+}
+
+tri_status brsi_inv(int64_t n, void *a, int64_t lda, int gamma, const int64_t *perm, tri_dtype dtype,
+                    void *stream) {
+    if (!valid_enums(TRI_LOWER, TRI_NONUNIT, dtype) || n < 0 || gamma < 2 || gamma > 16) return TRI_ERR_ARG;
+    if (n == 0) return TRI_OK;
+    if (!a || lda < std::max<int64_t>(1, n) || !valid_perm(n, perm)) return TRI_ERR_ARG;
+    if (n > 65535) return TRI_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    tri_status st = device_ctx(s, &c);
+    if (st != TRI_OK) return st;
+    const size_t need = brsi_ws_bytes(n, gamma, dtype);
+    void *ws = nullptr;
+    if (lib_malloc_async(&ws, need, s) != cudaSuccess) {
+        cudaGetLastError();
+        return TRI_ERR_NOMEM;
+    }
+    st = brsi_inv_ex(n, a, lda, gamma, perm, dtype, ws, need, nullptr, stream);
+    cudaError_t e = cudaFreeAsync(ws, s);
+    if (st == TRI_OK && e != cudaSuccess) st = TRI_ERR_CUDA;
+    return st;
+}
+
 size_t skul_workspace_size(int64_t n, tri_dtype dtype) {
     if (n <= 0 || !valid_enums(TRI_LOWER, TRI_NONUNIT, dtype)) return 0;
     return skul_ws_bytes(n, dtype);
@@ -553,6 +616,14 @@ tri_status tri_get_info(void *stream, int64_t *first_bad_index) {
     if (info != LLONG_MAX) return TRI_ERR_SINGULAR;
     return TRI_OK;
 }
+
+tri_status tri_set_growth_limit(double tau) {
+    if (tau != tau) return TRI_ERR_ARG;
+    g_growth_tau.store(tau > 0.0 ? (float)std::min(tau, 3.0e38) : 0.f, std::memory_order_relaxed);
+    return TRI_OK;
+}
+
+double tri_growth_limit(void) { return (double)g_growth_tau.load(std::memory_order_relaxed); }
 
 tri_status tri_pool_stats(uint64_t *used, uint64_t *used_high, int reset_high) {
     cudaMemPool_t pool;

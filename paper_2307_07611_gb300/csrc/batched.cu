@@ -113,33 +113,21 @@ __device__ __forceinline__ void write_planes(const T *tiles, int nt, int n, long
     }
 }
 
-// info_as >= 0: a zero pivot records info_as (the matrix of a batch) instead of the row.
-// S: the element type in global memory (T, or FP32 data inverted in FP64).
-// tau > 0 (FP32 only): growth limit.  When the FP32 inverse has max|X| * max|T| > tau and
-// the block has at most 128 rows, the block, still unchanged in global memory, is loaded
-// again and inverted in FP64 in the same shared memory, and that result is stored.
-template <typename T, bool TRANS, bool UNIT, int MAXT, int NT, typename S = T>
-__device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
-                                             __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
-                                             long long ldp, long long ntot, __nv_bfloat16 *q0 = nullptr,
-                                             __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr,
-                                             long long info_as = -1, float tau = 0.f) {
+// Loads the lower tiles of block d (strict upper of diagonal tiles = 0, padding =
+// identity), one warp per tile.  FP32 tiles that lie inside the block, from a 16-byte
+// aligned source with ld a multiple of 4, come in as 8 float4 loads per lane (lane = 4
+// consecutive elements along the contiguous index of the source); the rest as 32 scalar
+// loads per lane.  Returns this thread's max |element| seen.  No barrier.
+template <typename T, bool TRANS, bool UNIT, int NT, typename S>
+__device__ __forceinline__ float load_tiles(const BDesc &d, T *tiles) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = NT / 32;
     const int n = d.n, nt = (n + 31) / 32;
     const S *g = reinterpret_cast<const S *>(d.ptr);
     const long long ld = d.ld;
-    __shared__ unsigned s_tmax, s_xmax;      // max |T| and max |X| as float bits (tau > 0)
-    float tmax = 0.f;
-
-    // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
-    // One warp per tile.  FP32 tiles that lie inside the block, from a 16-byte aligned
-    // source with ld a multiple of 4, come in as 8 float4 loads per lane (lane = 4
-    // consecutive elements along the contiguous index of the source); the rest as 32
-    // scalar loads per lane.
     const int ntl = nt * (nt + 1) / 2;
     const bool vec_ok = sizeof(S) == 4 && (((uintptr_t)g & 15) == 0) && (ld % 4 == 0);
-    if (tau > 0.f && tid == 0) s_tmax = s_xmax = 0u;
+    float tmax = 0.f;
     for (int tl = warp; tl < ntl; tl += nwarps) {
         int I = 0;
         while ((I + 1) * (I + 2) / 2 <= tl) ++I;
@@ -192,6 +180,76 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             tmax = fmaxf(tmax, fabsf((float)v[q]));
         }
     }
+    return tmax;
+}
+
+// FP64 inverse of an ill-conditioned block of more than 128 rows whose FP32 source in
+// global memory is still unchanged (the FP64 tiles of such a block do not fit in shared
+// memory).  T is staged in shared memory as FP32 -- exact, it is FP32 data -- packed by
+// rows (row i at offset i(i+1)/2), and warp w computes the columns j = w, w + nwarps, ...
+// by the column recurrence of CRIT (Section 4.2) in FP64:
+//     x_jj = 1/t_jj,   x_ij = -(sum_{k=j}^{i-1} t_ik x_kj) / t_ii   (i > j),
+// each sum split over the lanes and reduced by shuffles; column j of X (FP64) lives in
+// the warp's slice of shared memory.  The result is stored rounded to FP32.  About 0.7 ms
+// per 256-row block on one SM (FP64 throughput), for blocks that need it only.
+// smem: at least n(n+1)/2 floats + NT/32 * 256 doubles.
+template <bool TRANS, bool UNIT, int NT>
+__device__ void redo_columns_fp64(const BDesc &d, uint8_t *smem) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+    const int n = d.n;
+    const long long ld = d.ld;
+    float *tp = reinterpret_cast<float *>(smem);
+    double *xs = reinterpret_cast<double *>(smem + (((size_t)n * (n + 1) / 2 * 4 + 15) / 16) * 16);
+    const float *g = reinterpret_cast<const float *>(d.ptr);
+    for (int i = warp; i < n; i += nwarps)
+        for (int k = lane; k <= i; k += 32)
+            tp[(size_t)i * (i + 1) / 2 + k] = (k == i && UNIT) ? 1.f : g[vidx<TRANS>(i, k, ld)];
+    __syncthreads();
+    float *go = reinterpret_cast<float *>(d.ptr);
+    double *x = xs + (size_t)warp * 256;
+    for (int j = warp; j < n; j += nwarps) {
+        if (lane == 0) x[j] = 1.0 / (double)tp[(size_t)j * (j + 1) / 2 + j];
+        __syncwarp();
+        for (int i = j + 1; i < n; ++i) {
+            const float *ti = tp + (size_t)i * (i + 1) / 2;
+            double acc = 0.0;
+            for (int k = j + lane; k < i; k += 32) acc = fma((double)ti[k], x[k], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) x[i] = -acc / (double)ti[i];
+            __syncwarp();
+        }
+        for (int i = j + lane; i < n; i += 32)
+            if (!(UNIT && i == j)) go[vidx<TRANS>(i, j, ld)] = (float)x[i];
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// info_as >= 0: a zero pivot records info_as (the matrix of a batch) instead of the row.
+// S: the element type in global memory (T, or FP32 data inverted in FP64).
+// tau > 0 (FP32 only): growth limit.  When the FP32 inverse has max|X| * max|T| > tau and
+// the block has at most 128 rows, the block, still unchanged in global memory, is loaded
+// again and inverted in FP64 in the same shared memory, and that result is stored.
+template <typename T, bool TRANS, bool UNIT, int MAXT, int NT, typename S = T>
+__device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, long long *info, long long row0,
+                                             __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2,
+                                             long long ldp, long long ntot, __nv_bfloat16 *q0 = nullptr,
+                                             __nv_bfloat16 *q1 = nullptr, __nv_bfloat16 *q2 = nullptr,
+                                             long long info_as = -1, float tau = 0.f, int *redo_flag = nullptr) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = NT / 32;
+    const int n = d.n, nt = (n + 31) / 32;
+    const S *g = reinterpret_cast<const S *>(d.ptr);
+    const long long ld = d.ld;
+    __shared__ unsigned s_tmax, s_xmax;      // max |T| and max |X| as float bits (tau > 0)
+
+    // Load the lower tiles (strict upper of diagonal tiles = 0, padding = identity).
+    const int ntl = nt * (nt + 1) / 2;
+    const bool vec_ok = sizeof(S) == 4 && (((uintptr_t)g & 15) == 0) && (ld % 4 == 0);
+    if (tau > 0.f && tid == 0) s_tmax = s_xmax = 0u;
+    const float tmax = load_tiles<T, TRANS, UNIT, NT, S>(d, tiles);
     __syncthreads();
     if (tau > 0.f) atomicMax(&s_tmax, __float_as_uint(tmax));   // non-negative: bit order = value order
 
@@ -209,7 +267,8 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     }
 
     if constexpr (std::is_same<T, float>::value) {
-        if (tau > 0.f && n <= 128) {   // larger blocks keep the FP32 result: no scan
+        bool redo = false;
+        if (tau > 0.f) {
             float xmax = 0.f;
             for (int x = tid; x < ntl * 1024; x += NT) {
                 const int tl = x / 1024, e = x % 1024;
@@ -219,15 +278,32 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             __syncthreads();
             const float growth = __uint_as_float(s_xmax) * __uint_as_float(s_tmax);
             __syncthreads();
-            if (!(growth <= tau)) {
-                // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
-                // the shared memory of the FP32 block
-                double *dt = reinterpret_cast<double *>(tiles);
-                invert_block<double, TRANS, UNIT, 4, NT, float>(d, dt, dt + (size_t)BLimits<4>::kTiles * TE, info,
-                                                                row0, nullptr, nullptr, nullptr, 0, ntot, nullptr,
-                                                                nullptr, nullptr, info_as, 0.f);
-                return;
+            redo = !(growth <= tau);
+        }
+        if (redo_flag && tid == 0) *redo_flag = redo ? 1 : 0;
+        if (redo && n <= 128) {
+            // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
+            // the shared memory of the FP32 block
+            double *dt = reinterpret_cast<double *>(tiles);
+            invert_block<double, TRANS, UNIT, 4, NT, float>(d, dt, dt + (size_t)BLimits<4>::kTiles * TE, info,
+                                                            row0, nullptr, nullptr, nullptr, 0, ntot, nullptr,
+                                                            nullptr, nullptr, info_as, 0.f);
+            if (p0 != nullptr) {
+                load_tiles<float, TRANS, UNIT, NT, S>(d, tiles);
+                __syncthreads();
+                write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
             }
+            return;
+        }
+        if (redo) {
+            // FP64 column recurrence from the unchanged source, stored directly
+            redo_columns_fp64<TRANS, UNIT, NT>(d, reinterpret_cast<uint8_t *>(tiles));
+            if (p0 != nullptr) {
+                load_tiles<float, TRANS, UNIT, NT, S>(d, tiles);
+                __syncthreads();
+                write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
+            }
+            return;
         }
     }
 
@@ -292,12 +368,15 @@ __global__ void __launch_bounds__(NT, 1) batched_kernel(const BDesc *__restrict_
 // BF16 planes of that diagonal block.  blockIdx.y: matrix of a batch (matrices as_, planes
 // ps elements apart); index0 >= 0: a zero pivot records the matrix index index0 + blockIdx.y
 // instead of the row.
+// tau > 0: growth limit; a block whose FP32 inverse has max|X| max|T| > tau is inverted
+// again in FP64 and flags[blockIdx.y * gridDim.x + blockIdx.x] is set to 1 (else 0).
 template <bool TRANS, bool UNIT>
 __global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long lda, long long n, long long *info,
                                                              __nv_bfloat16 *p0, __nv_bfloat16 *p1,
                                                              __nv_bfloat16 *p2, long long ldp, __nv_bfloat16 *q0,
                                                              __nv_bfloat16 *q1, __nv_bfloat16 *q2,
-                                                             long long as_, long long ps, long long index0) {
+                                                             long long as_, long long ps, long long index0,
+                                                             float tau, int *flags) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
     float *wt = tiles + (size_t)BLimits<8>::kTiles * TE;
@@ -310,7 +389,8 @@ __global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long
     }
     BDesc d{a + vidx<TRANS>(r0, r0, lda), lda, (int)min(256ll, n - r0), (int)blockIdx.x};
     invert_block<float, TRANS, UNIT, 8, 512>(d, tiles, wt, info, r0, p0, p1, p2, ldp, n, q0, q1, q2,
-                                             index0 >= 0 ? index0 + mb : -1);
+                                             index0 >= 0 ? index0 + mb : -1, tau,
+                                             flags ? flags + mb * gridDim.x + blockIdx.x : nullptr);
 }
 
 template <typename T, int MAXT>
@@ -344,7 +424,7 @@ KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *sme
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
                                __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
                                __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2, int64_t batch,
-                               int64_t as_, int64_t ps, int64_t index0) {
+                               int64_t as_, int64_t ps, int64_t index0, float tau, int *flags) {
     const int64_t blocks = (n + 255) / 256;
     if (blocks <= 0 || batch <= 0) return cudaSuccess;
     if (batch > 65535) return cudaErrorInvalidValue;
@@ -360,7 +440,7 @@ cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, f
     }
     TraceScope ts(c.stream, "diag_blocks", fl * (double)batch, (double)batch * n * 256.0 * (4.0 + 4.0 + 6.0));
     k<<<dim3((unsigned)blocks, (unsigned)batch), 512, smem, c.stream>>>(a, lda, n, c.info, p0, p1, p2, ldp, q0, q1,
-                                                                       q2, as_, ps, index0);
+                                                                       q2, as_, ps, index0, tau, flags);
     return cudaGetLastError();
 }
 

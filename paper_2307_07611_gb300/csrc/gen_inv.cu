@@ -44,7 +44,8 @@ namespace {
 // block are written back over it (L strictly below the diagonal, U on and above it).
 template <typename T, int L, int NT>
 __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T *__restrict__ ks, int64_t ldk,
-                                                     int64_t off, int nb, long long *info, T *lu_out) {
+                                                     int64_t off, int nb, long long *info, T *lu_out,
+                                                     long long info_base) {
     constexpr int NW = NT / 32;
     constexpr int WC = 4, WR = NW / WC;          // grid of warp sub-blocks
     constexpr int BR = L / WR, BC = L / WC;      // sub-block of a warp
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(NT) lu_leaf_kernel(const T *a, int64_t lda, T 
         __syncthreads();
     }
     for (int k = tid; k < nb; k += NT)
-        if (pv[k] == T(0) || !isfinite(pv[k])) atomicMin(info, (long long)(off + k));
+        if (pv[k] == T(0) || !isfinite(pv[k])) atomicMin(info, info_base + (long long)(off + k));
     if (lu_out)
         for (int idx = tid; idx < nb * nb; idx += NT) {
             const int i = idx % nb, j = idx / nb;
@@ -271,6 +272,7 @@ struct GenCtx {
     GenLayout lay;
     int L;
     bool keep = false;   // write L21, U12 and the leaf factors back over A (SKUL)
+    long long info_base = 0;   // added to the reported pivot index (a block of a larger matrix)
 };
 
 // Mixed products: three terms (about 2^-16 relative) in gen_inv, whose Newton-Schulz step
@@ -293,7 +295,7 @@ cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int6
         if (e != cudaSuccess) return e;
         lu_leaf_kernel<double, L, NT><<<1, NT, sm, g.c->stream>>>((const double *)a, lda, (double *)ks, ldk,
                                                                   off, nb, g.c->info,
-                                                                  g.keep ? (double *)a : nullptr);
+                                                                  g.keep ? (double *)a : nullptr, g.info_base);
     } else {
         constexpr int L = 128, NT = 512;
         constexpr size_t sm = lu_leaf_smem<float, L>();
@@ -301,7 +303,8 @@ cudaError_t launch_leaf_lu(const GenCtx &g, void *a, int64_t lda, void *ks, int6
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         lu_leaf_kernel<float, L, NT><<<1, NT, sm, g.c->stream>>>((const float *)a, lda, (float *)ks, ldk, off,
-                                                                 nb, g.c->info, g.keep ? (float *)a : nullptr);
+                                                                 nb, g.c->info, g.keep ? (float *)a : nullptr,
+                                                                 g.info_base);
     }
     return cudaGetLastError();
 }
@@ -385,6 +388,9 @@ size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt) {
     return gen_layout(n, dt).total;
 }
 
+tri_status dense_newton_schulz(const Ctx &c, int64_t n, const float *a, int64_t lda, float *x, int64_t ldx,
+                               float *r, int64_t ldr, void *planes);
+
 // TRI_F32_MIXED with n >= kTcMin ends with one Newton-Schulz step on the dense inverse,
 //     R = I - A X     six promoted terms (FP32 class; R is a difference of nearly equal
 //                     quantities, so it needs the full 24 bits of A and X)
@@ -392,8 +398,9 @@ size_t gen_inv_ws_bytes(int64_t n, tri_dtype dt) {
 //                     BF16 error of this product is far below FP32 rounding of X
 // which brings the normwise residual from the three-term products' level to FP32 level.
 // R is written over the K\S buffer, which the final product has consumed.
-tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws) {
+tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t lda, void *ws, int64_t info_base) {
     GenCtx g{&c, dt, (uint8_t *)ws, gen_layout(n, dt), leaf_size(dt)};
+    g.info_base = info_base;
     uint8_t *ks = (uint8_t *)ws;
     const int64_t ldk = n;
     const bool ns = g.lay.a0 > 0;
@@ -407,12 +414,18 @@ tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t l
     e = product(g, GemmArgs{n, n, n, 1.0, ks, ldk, OP_UPPER, ks, ldk, OP_LOWER_UNIT, 0.0, a, lda, OP_FULL},
                 "gen:sk");
     if (e != cudaSuccess || !ns) return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
-    void *planes = g.ws + g.lay.ks + g.lay.temps;
-    GemmArgs r{n, n, n, -1.0, a0, n, OP_FULL, a, lda, OP_FULL, 0.0, ks, ldk, OP_FULL};
-    r.dadd = 1.0;
-    e = gemm_tc(c, r, 6, planes, "gen:ns_res");
+    return dense_newton_schulz(c, n, a0, n, (float *)a, lda, (float *)ks, ldk, g.ws + g.lay.ks + g.lay.temps);
+}
+
+// One Newton-Schulz step on a dense FP32 inverse X of A: R = I - A X (six promoted
+// split-BF16 terms) into r, then X += X R (one term).  planes: gemm_tc_ws_bytes(n, n, n).
+tri_status dense_newton_schulz(const Ctx &c, int64_t n, const float *a, int64_t lda, float *x, int64_t ldx,
+                               float *r, int64_t ldr, void *planes) {
+    GemmArgs g{n, n, n, -1.0, a, lda, OP_FULL, x, ldx, OP_FULL, 0.0, r, ldr, OP_FULL};
+    g.dadd = 1.0;
+    cudaError_t e = gemm_tc(c, g, 6, planes, "gen:ns_res");
     if (e != cudaSuccess) return TRI_ERR_CUDA;
-    e = gemm_tc(c, GemmArgs{n, n, n, 1.0, a, lda, OP_FULL, ks, ldk, OP_FULL, 1.0, a, lda, OP_FULL}, 1, planes,
+    e = gemm_tc(c, GemmArgs{n, n, n, 1.0, x, ldx, OP_FULL, r, ldr, OP_FULL, 1.0, x, ldx, OP_FULL}, 1, planes,
                 "gen:ns_upd");
     return e == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }

@@ -16,6 +16,8 @@ struct Ctx {
     int *timeout;      // device: set to 1 when a bounded wait runs out
     int sm_count;
     int device;
+    float tau;         // growth limit of the FP64 fallback for ill-conditioned diagonal
+                       // blocks (tri_set_growth_limit; <= 0 disables)
 };
 
 // Lower-orientation view of a column-major matrix.  For an upper-triangular matrix U

@@ -40,7 +40,7 @@ cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_o
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
                                __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
                                __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2, int64_t batch,
-                               int64_t as_, int64_t ps, int64_t index0);
+                               int64_t as_, int64_t ps, int64_t index0, float tau, int *flags);
 
 // Per-device side stream and events used to run two independent kernels concurrently
 // (fork / join through events, so the pair also works inside stream capture).
@@ -81,12 +81,13 @@ struct Layout {
     int64_t ldp;
     size_t plane;                 // bytes of one plane of one matrix (256-aligned)
     int64_t batch;                // matrices whose planes the workspace holds
-    size_t off_t, off_x, off_r, off_w, off_f, total;
+    size_t off_t, off_x, off_r, off_w, off_f, off_g, total;
 };
 
 // Workspace: T planes (3), X planes (3), R plane, W planes (2; single matrix: at the
 // positions of the B blocks of T; batch: the compact h x P*h level layout), each a group of
-// `batch` planes, then the ready counters of the single-launch schedule.
+// `batch` planes, then the ready counters of the single-launch schedule, then one growth
+// flag per diagonal block of every matrix.
 Layout layout(int64_t n, int64_t batch = 1) {
     Layout L{};
     L.ldp = round_up(std::max<int64_t>(n, 1), 64);
@@ -98,7 +99,8 @@ Layout layout(int64_t n, int64_t batch = 1) {
     L.off_r = L.off_x + 3 * g;
     L.off_w = L.off_r + g;
     L.off_f = L.off_w + 2 * g;
-    L.total = L.off_f + al256(tc::graph_flag_bytes(n));
+    L.off_g = L.off_f + al256(tc::graph_flag_bytes(n));
+    L.total = L.off_g + al256((size_t)((n + kDiag - 1) / kDiag) * (size_t)batch * sizeof(int));
     return L;
 }
 
@@ -120,7 +122,9 @@ struct Launch {
 // TRI_LEVEL_TILE_N="h:bn,..." (bn in {64, 128, 256}) overrides the table, read once.
 int level_tile_n(int64_t h) {
     static const std::vector<std::pair<int64_t, int>> table = [] {
-        std::vector<std::pair<int64_t, int>> t;
+        // measured at n = 8192 (one GB300, untraced step): all 256 wide 1.436 ms; this
+        // table 1.416 ms; 128 wide from h = 2048 up, or 64 wide at h = 1024, were slower
+        std::vector<std::pair<int64_t, int>> t = {{256, 64}, {512, 128}, {1024, 128}};
         if (const char *e = std::getenv("TRI_LEVEL_TILE_N")) {
             t.clear();
             long long hh = 0;
@@ -316,8 +320,11 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps) !=
         cudaSuccess)
         return TRI_ERR_CUDA;
+    // growth flags of the diagonal blocks (the single-launch schedule takes no fallback)
+    int *gflags = (int *)(base + L.off_g);
+    const float tau = graph ? 0.f : c.tau;
     if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2], batch, stride, ps,
-                           index0) != cudaSuccess)
+                           index0, tau, tau > 0.f ? gflags : nullptr) != cudaSuccess)
         return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
@@ -362,6 +369,10 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
     tc::Epi er{nullptr, 0, R[0], nullptr, nullptr, L.ldp, n, n};
     er.os = ps;
+    if (tau > 0.f) {
+        er.skip = gflags;
+        er.skip_n = (int)((n + kDiag - 1) / kDiag);
+    }
     if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
                       plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
         return TRI_ERR_CUDA;

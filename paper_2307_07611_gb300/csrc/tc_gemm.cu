@@ -51,9 +51,10 @@ struct Maps {
 // Stores NC accumulator columns gn0..gn0+NC-1 of row gm (one thread = one row).
 // Column-major targets advance by one leading dimension per column, so the 32 threads of
 // a warp (32 consecutive rows) write contiguous bytes for every column.
+// zero (MODE_RES): write R = 0 (the matrix skips its Newton-Schulz step).
 template <int MODE, bool TRANS, bool UNIT, int NC>
 __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t ob, int64_t gm, int64_t gn0,
-                                              const uint32_t (&r)[NC]) {
+                                              const uint32_t (&r)[NC], bool zero = false) {
     if (gm >= ep.mlim) return;
     const int64_t left = ep.nlim - gn0;
     if (MODE == MODE_W || MODE == MODE_X21 || MODE == MODE_RES) {
@@ -70,7 +71,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
                     ep.x[xo] = v;
                 } else if (MODE == MODE_RES) {
                     const int64_t gn = gn0 + j;
-                    v = gm >= gn ? ((gm == gn ? 1.f : 0.f) - acc) : 0.f;
+                    v = (gm >= gn && !zero) ? ((gm == gn ? 1.f : 0.f) - acc) : 0.f;
                 }
                 const __nv_bfloat16 h = __float2bfloat16_rn(v);
                 const float r1 = v - __bfloat162float(h);
@@ -451,12 +452,20 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                 if (lane == 0) mbar_arrive(tempty_bar(a));
             }
             if (PROMOTE && ok) {
+                // a matrix whose diagonal block needed the FP64 fallback skips its step
+                bool zero = false;
+                if (MODE == MODE_RES && ep.skip) {
+                    int f = 0;
+                    for (int i = lane; i < ep.skip_n; i += 32) f |= ep.skip[(int64_t)tl.b * ep.skip_n + i];
+                    zero = __any_sync(0xffffffffu, f != 0);
+                }
 #pragma unroll
                 for (int q = 0; q < BNT / 32; ++q) {
                     uint32_t r[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(sum[q * 16 + i]);
-                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, xb, ob, gm, (int64_t)tl.on + half * (BNT / 2) + q * 16, r);
+                    epilogue_cols<MODE, TRANS, UNIT, 16>(ep, xb, ob, gm, (int64_t)tl.on + half * (BNT / 2) + q * 16, r,
+                                                         zero);
                 }
             }
         }

@@ -42,6 +42,8 @@ struct Epi {
                                    // 3 / 4 strict lower / upper with a zero diagonal
     float dadd = 0.f;              // MODE_GEN (cmask 0..2): added to diagonal entries
     int64_t xs = 0, os = 0;        // batch strides (elements) of x and of the output planes
+    const int *skip = nullptr;     // MODE_RES: skip_n flags per matrix of the batch; a matrix
+    int skip_n = 0;                // with a flag set gets R = 0 (its Newton-Schulz step is a no-op)
 };
 
 enum Mode {

@@ -66,6 +66,9 @@ def _declare(lib):
         "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
         "gen_inv_ex": ([i64, vp, i64, i32, vp, sz, vp, vp], i32),
+        "brsi_inv": ([i64, vp, i64, i32, ctypes.POINTER(i64), i32, vp], i32),
+        "brsi_inv_workspace_size": ([i64, i32, i32], sz),
+        "brsi_inv_ex": ([i64, vp, i64, i32, ctypes.POINTER(i64), i32, vp, sz, vp, vp], i32),
         "skul": ([i64, vp, i64, vp, i64, i32, vp], i32),
         "skul_workspace_size": ([i64, i32], sz),
         "skul_ex": ([i64, vp, i64, vp, i64, i32, vp, sz, vp, vp], i32),
@@ -78,6 +81,8 @@ def _declare(lib):
         "tri_mixed_schedule_stats": ([i64, i32, ctypes.POINTER(ctypes.c_double), i32], i32),
         "tri_batched_partition": ([i64, ctypes.POINTER(i64), i32, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_double)], i32),
+        "tri_set_growth_limit": ([ctypes.c_double], i32),
+        "tri_growth_limit": ([], ctypes.c_double),
         "tri_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "tri_pool_stats": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), i32], i32),
         "tri_trace_enable": ([i32], None),
@@ -143,6 +148,26 @@ def gen_inv_workspace_size(n, dtype) -> int:
 
 def gen_inv_ex(n, ptr, ld, dtype, workspace, ws_bytes, stream=0, d_info=0) -> int:
     return load().gen_inv_ex(n, ptr, ld, dtype, workspace or None, ws_bytes, d_info or None, stream or None)
+
+
+def _perm_arg(perm):
+    if perm is None:
+        return None
+    return (ctypes.c_int64 * max(len(perm), 1))(*[int(p) for p in perm])
+
+
+def brsi_inv(n, ptr, ld, gamma, dtype, perm=None, stream=0) -> int:
+    """BRSI(gamma) general inverse in place; perm: the column permutation P_0 (host list)."""
+    return load().brsi_inv(n, ptr, ld, int(gamma), _perm_arg(perm), dtype, stream or None)
+
+
+def brsi_inv_workspace_size(n, gamma, dtype) -> int:
+    return int(load().brsi_inv_workspace_size(n, int(gamma), dtype))
+
+
+def brsi_inv_ex(n, ptr, ld, gamma, dtype, workspace, ws_bytes, perm=None, stream=0, d_info=0) -> int:
+    return load().brsi_inv_ex(n, ptr, ld, int(gamma), _perm_arg(perm), dtype, workspace or None, ws_bytes,
+                              d_info or None, stream or None)
 
 
 def skul(n, a_ptr, lda, sk_ptr, ldsk, dtype, stream=0) -> int:
@@ -302,6 +327,14 @@ def tri_get_info(stream=0):
     idx = ctypes.c_int64(-1)
     st = load().tri_get_info(stream or None, ctypes.byref(idx))
     return st, idx.value
+
+
+def tri_set_growth_limit(tau: float) -> int:
+    return load().tri_set_growth_limit(float(tau))
+
+
+def tri_growth_limit() -> float:
+    return float(load().tri_growth_limit())
 
 
 def tri_alu_peak(dtype, iters: int = 1 << 16):

@@ -221,14 +221,29 @@ def test_batched_growth_limit_power_of_two_block(lib):
 
 
 def test_batched_growth_limit_leaves_the_rest_alone(lib):
-    """Well-conditioned blocks (the batched law) and blocks above 128 rows keep the FP32
-    result: bit-identical with the limit on and off."""
-    blocks = [inputs.tri_lower(n, seed=n).astype(np.float64) for n in (40, 128, 200)]
-    blocks.append(_ill_block(200, 0.5, 7))
+    """Well-conditioned blocks (the batched law), up to 256 rows, keep the FP32 result:
+    bit-identical with the limit on and off."""
+    blocks = [inputs.tri_lower(n, seed=n).astype(np.float64) for n in (40, 128, 200, 256)]
     on = _run_plan(lib, blocks, None, False)
     off = _run_plan(lib, blocks, 0.0, False)
     for a, b in zip(on, off):
         assert np.array_equal(a, b)
+
+
+def test_batched_growth_limit_large_blocks(lib):
+    """Ill-conditioned blocks of 129..256 rows (their FP64 tiles do not fit in shared
+    memory) are inverted again by the FP64 column recurrence from the unchanged source:
+    entrywise within 2^-23 of the FP64 oracle, against far worse without the limit; the
+    well-conditioned block beside them is untouched."""
+    blocks = [_ill_block(200, 0.5, 7), _ill_block(256, 0.45, 8), inputs.tri_lower(180, seed=9).astype(np.float64)]
+    on = _run_plan(lib, blocks, None, True)
+    off = _run_plan(lib, blocks, 0.0, True)
+    for x_on, x_off, t in zip(on[:2], off[:2], blocks[:2]):
+        e_on, e_off = _entry_rel_err(x_on, t), _entry_rel_err(x_off, t)
+        assert e_on <= 2.0 ** -23, e_on
+        assert e_off > 10 * e_on, (e_off, e_on)
+    assert np.array_equal(on[2], off[2])
+    assert lib.tri_get_info()[0] == lib.TRI_OK
 
 
 def test_batched_growth_limit_errors(lib):
