@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--cpu-sample-stride", type=int, default=1)
     p.add_argument("--profile-config", default=None,
                    choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512",
-                            "combrit_beta", "factor_f32_n16384", "factor_f32_n2048"],
+                            "combrit_beta", "factor_f32_n16384", "factor_f32_n2048", "brsi_gamma"],
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
@@ -448,7 +448,7 @@ def _secondary_factor(torch, lib, dev, out, only):
     import numpy as np
     from paper_2307_07611_gb300 import inputs
     if only is not None and only not in ("factor_f32_n16384", "factor_f32_n2048"):
-        return out
+        return _secondary_brsi(torch, lib, dev, out, only)
     sh = int(torch.cuda.current_stream().cuda_stream)
     n = 2048 if only == "factor_f32_n2048" else 16384   # the small case is for profiler captures
     a = inputs.general(n, seed=0, dtype=np.float32)
@@ -499,6 +499,56 @@ def _secondary_factor(torch, lib, dev, out, only):
     res["unit"] = "TFLOP/s (7n^3/3: MGS QR 2n^3 plus S n^3/3)"
     out[f"sqr_f32_n{n}"] = res
     del pr, wk, sk, rr
+    torch.cuda.empty_cache()
+    return _secondary_brsi(torch, lib, dev, out, only)
+
+
+def _secondary_brsi(torch, lib, dev, out, only):
+    """BRSI with gamma blocks (Section 5.2) on the general law, n = 4096: time and
+    residual per gamma, mixed and plain FP32, next to gen_inv (the two-block LU route).
+    The paper's complexity analysis predicts the cost to grow with gamma."""
+    import numpy as np
+    from paper_2307_07611_gb300 import inputs
+    if only is not None and only != "brsi_gamma":
+        return out
+    sh = int(torch.cuda.current_stream().cuda_stream)
+    n = 4096
+    a = inputs.general(n, seed=0, dtype=np.float32)
+    pr = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
+    wk = torch.empty_like(pr)
+    ad = pr.T.double()
+    cols = [0, n // 2, n - 1]
+
+    def col_res():
+        x = wk[cols, :].double()
+        rr = ad @ x.T
+        for k, c in enumerate(cols):
+            rr[c, k] -= 1.0
+        return max(float(rr[:, k].norm() / (ad.norm() * x[k].norm())) for k in range(len(cols)))
+
+    res = {}
+    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32)):
+        row = {}
+        for gamma in (2, 3, 4, 8):
+            need = lib.brsi_inv_workspace_size(n, gamma, code)
+            ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+            wp = (ws.data_ptr() + 255) // 256 * 256
+            ms = event_time(torch, lambda: lib.check(lib.brsi_inv_ex(n, wk.data_ptr(), n, gamma, code, wp, need,
+                                                                     stream=sh)), 2, 1, setup=lambda: wk.copy_(pr))
+            row[f"gamma{gamma}"] = {"ms": ms, "value": n ** 3 / (ms * 1e-3) / 1e12,
+                                    "sampled_column_residual_max": col_res()}
+            del ws
+        need = lib.gen_inv_workspace_size(n, code)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        wp = (ws.data_ptr() + 255) // 256 * 256
+        ms = event_time(torch, lambda: lib.check(lib.gen_inv_ex(n, wk.data_ptr(), n, code, wp, need, sh)), 2, 1,
+                        setup=lambda: wk.copy_(pr))
+        row["gen_inv"] = {"ms": ms, "value": n ** 3 / (ms * 1e-3) / 1e12, "sampled_column_residual_max": col_res()}
+        del ws
+        res[name] = row
+    res["unit"] = "TFLOP/s (n^3)"
+    out[f"brsi_f32_n{n}"] = res
+    del pr, wk
     torch.cuda.empty_cache()
     return out
 

@@ -204,3 +204,18 @@ def test_sqr_argument_errors_need_no_gpu(libtri):
 
 def test_batched_growth_limit_null_plan_needs_no_gpu(libtri):
     assert lib.tri_batched_plan_set_growth_limit(None, 1e4) == lib.TRI_ERR_ARG
+
+
+def test_brsi_argument_errors_need_no_gpu(libtri):
+    A = lib.TRI_ERR_ARG
+    assert lib.brsi_inv(-1, 4096, 1, 2, lib.TRI_F32) == A
+    assert lib.brsi_inv(5, 4096, 5, 1, lib.TRI_F32) == A
+    assert lib.brsi_inv(5, 4096, 5, 17, lib.TRI_F32) == A
+    assert lib.brsi_inv(5, 0, 5, 2, lib.TRI_F32) == A
+    assert lib.brsi_inv(5, 4096, 5, 2, lib.TRI_F32, perm=[0, 0, 1, 2, 3]) == A
+    assert lib.brsi_inv(5, 4096, 5, 2, 9) == A
+    assert lib.brsi_inv_workspace_size(100, 1, lib.TRI_F32) == 0
+    need = lib.brsi_inv_workspace_size(100, 4, lib.TRI_F32)
+    assert need >= 4 * 100 * 100 * 4
+    assert lib.brsi_inv_ex(100, 4096, 100, 4, lib.TRI_F32, 256, need - 1) == lib.TRI_ERR_NOMEM
+
