@@ -456,6 +456,21 @@ TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
 TRI_API tri_status tri_set_growth_limit(double tau);
 TRI_API double tri_growth_limit(void);
 
+/* Recipe of TRI_F32_MIXED on the triangular paths (tri_inv[_ex], strided batches),
+ * process-wide:
+ *   TRI_RECIPE_NEWTON_SCHULZ (default)  three-term split-BF16 level products, then one
+ *       Newton-Schulz step X <- X + X (I - T X) with a six-term residual and a one-term
+ *       update: the result is better than the plain FP32 recursion's.
+ *   TRI_RECIPE_DIRECT  the level products take all six split-BF16 terms with FP32
+ *       promotion every 64 k (FP32-class products) and there is no Newton-Schulz step:
+ *       about the plain FP32 recursion's accuracy, at about 60% of the tensor-core work.
+ *       Not part of the paper's method or of the spec recipe; an alternative.
+ * Errors: TRI_ERR_ARG (unknown recipe). */
+#define TRI_RECIPE_NEWTON_SCHULZ 0
+#define TRI_RECIPE_DIRECT 1
+TRI_API tri_status tri_set_mixed_recipe(int recipe);
+TRI_API int tri_mixed_recipe(void);
+
 /* Measured CUDA-core peak of the current device for dtype TRI_F32 (FFMA) or TRI_F64
  * (DFMA), in TFLOP/s (2 flops per fused multiply-add): every thread of a full grid runs 8
  * independent chains of `iters` dependent FMAs, timed with CUDA events after a warm-up.

@@ -46,6 +46,9 @@ DeviceState g_dev[64];
 // triggers an FP64 inverse of that block.  Process-wide; <= 0 disables.
 std::atomic<float> g_growth_tau{1.0e4f};
 
+// Recipe of the mixed triangular path (process-wide).
+std::atomic<int> g_recipe{TRI_RECIPE_NEWTON_SCHULZ};
+
 tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TRI_ERR_CUDA;
@@ -67,6 +70,7 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     out->sm_count = d.sm_count;
     out->device = dev;
     out->tau = g_growth_tau.load(std::memory_order_relaxed);
+    out->recipe = g_recipe.load(std::memory_order_relaxed);
     return TRI_OK;
 }
 
@@ -624,6 +628,14 @@ tri_status tri_set_growth_limit(double tau) {
 }
 
 double tri_growth_limit(void) { return (double)g_growth_tau.load(std::memory_order_relaxed); }
+
+tri_status tri_set_mixed_recipe(int recipe) {
+    if (recipe != TRI_RECIPE_NEWTON_SCHULZ && recipe != TRI_RECIPE_DIRECT) return TRI_ERR_ARG;
+    g_recipe.store(recipe, std::memory_order_relaxed);
+    return TRI_OK;
+}
+
+int tri_mixed_recipe(void) { return g_recipe.load(std::memory_order_relaxed); }
 
 tri_status tri_pool_stats(uint64_t *used, uint64_t *used_high, int reset_high) {
     cudaMemPool_t pool;

@@ -251,7 +251,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
     if (tau > 0.f && tid == 0) s_tmax = s_xmax = 0u;
     const float tmax = load_tiles<T, TRANS, UNIT, NT, S>(d, tiles);
     __syncthreads();
-    if (tau > 0.f) atomicMax(&s_tmax, __float_as_uint(tmax));   // non-negative: bit order = value order
+    if (tau > 0.f) block_max_nonneg(&s_tmax, tmax);
 
     // Planes of T itself (diagonal blocks of the mixed path), before inverting.
     if (q0 != nullptr) {
@@ -274,7 +274,7 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
                 const int tl = x / 1024, e = x % 1024;
                 xmax = fmaxf(xmax, fabsf(tiles[(size_t)tl * TE + (e / 32) * TP + e % 32]));
             }
-            atomicMax(&s_xmax, __float_as_uint(xmax));
+            block_max_nonneg(&s_xmax, xmax);
             __syncthreads();
             const float growth = __uint_as_float(s_xmax) * __uint_as_float(s_tmax);
             __syncthreads();

@@ -202,6 +202,183 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, T alpha, const T *__restrict__
     }
 }
 
+// FP32, 128 x 128 output tile, 16-wide k steps, both operands column-major without a
+// transpose (the plain path's level products of lower matrices, the general inverse's
+// products): 16-byte loads of whole 4-element groups along each operand's contiguous
+// index (A along m, B along k).  A k step whose tile lies inside both operands' stored
+// triangles and inside the matrix is loaded without masks; the others (diagonal tiles,
+// ragged edges) go through per-element masks.  The host picks this kernel only when
+// every group is 16-byte aligned (base pointers, leading dimensions and batch strides
+// multiples of 4 elements).
+constexpr int VBM = 128, VBN = 128, VBK = 16, VNT = 256;
+
+__global__ void __launch_bounds__(VNT, 2)
+gemm_simt_vec_kernel(int64_t M, int64_t N, int64_t K, float alpha, const float *__restrict__ A, int64_t lda,
+                     int akind, const float *__restrict__ B, int64_t ldb, int bkind, float beta, float *C,
+                     int64_t ldc, int cmask, int64_t sa, int64_t sb, int64_t sc, int64_t nb1, int64_t sa2,
+                     int64_t sb2, int64_t sc2, int ksplit) {
+    __shared__ __align__(16) float As[2][VBK][VBM + 4];
+    __shared__ __align__(16) float Bs[2][VBK][VBN + 4];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * VBM;
+    const int n0 = blockIdx.x * VBN;
+    if (m0 >= M || n0 >= N) return;
+    const int ks = (int)(blockIdx.z % ksplit);
+    {
+        const int64_t z = blockIdx.z / ksplit;
+        const int64_t inner = z % nb1, outer = z / nb1;
+        A += inner * sa + outer * sa2;
+        B += inner * sb + outer * sb2;
+        C += inner * sc + outer * sc2;
+    }
+    const bool c_low = cmask == OP_LOWER || cmask == OP_LOWER_UNIT;
+    const bool c_up = cmask == OP_UPPER || cmask == OP_UPPER_UNIT;
+    if (c_low && n0 > m0 + VBM - 1) return;
+    if (c_up && m0 > n0 + VBN - 1) return;
+    const bool a_low = (akind == OP_LOWER || akind == OP_LOWER_UNIT);
+    const bool a_up = (akind == OP_UPPER || akind == OP_UPPER_UNIT);
+    const bool b_low = (bkind == OP_LOWER || bkind == OP_LOWER_UNIT);
+    const bool b_up = (bkind == OP_UPPER || bkind == OP_UPPER_UNIT);
+    const bool a_unit = akind == OP_LOWER_UNIT || akind == OP_UPPER_UNIT;
+    const bool b_unit = bkind == OP_LOWER_UNIT || bkind == OP_UPPER_UNIT;
+    int kbeg = 0, kend = (int)K;
+    if (a_low) kend = min(kend, m0 + VBM);
+    if (a_up) kbeg = max(kbeg, (m0 / VBK) * VBK);
+    if (b_low) kbeg = max(kbeg, (n0 / VBK) * VBK);
+    if (b_up) kend = min(kend, n0 + VBN);
+    if (ksplit > 1) {
+        const int len = ((kend - kbeg + ksplit - 1) / ksplit + VBK - 1) / VBK * VBK;
+        const int kb = kbeg + ks * len;
+        kend = min(kend, kb + len);
+        kbeg = kb;
+        if (kbeg >= kend) return;
+    }
+    const int Mi = (int)M, Ni = (int)N;
+    // A: thread -> rows am..am+3 (one 16-byte group), k rows ak and ak + 8 of the step
+    const int am = (tid & 31) * 4, ak = tid >> 5;
+    // B: thread -> k rows bk..bk+3 (one group), columns bn and bn + 64
+    const int bk = (tid & 3) * 4, bn = tid >> 2;
+    const bool m_full = m0 + VBM <= Mi, n_full = n0 + VBN <= Ni;
+    float4 ra[2], rb[2];
+    auto gload = [&](int kt) {
+        // whole step inside the stored triangles and the matrix: no masks
+        bool fast = kt + VBK <= kend;
+        if (a_low) fast = fast && kt + VBK <= m0 + (a_unit ? 0 : 1);      // k <= m (k < m for unit)
+        if (a_up) fast = fast && kt >= m0 + VBM - (a_unit ? 0 : 1);
+        if (b_low) fast = fast && kt >= n0 + VBN - (b_unit ? 0 : 1);
+        if (b_up) fast = fast && kt + VBK <= n0 + (b_unit ? 0 : 1);
+        if (fast && m_full) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                ra[h] = *reinterpret_cast<const float4 *>(A + (m0 + am) + (int64_t)(kt + ak + 8 * h) * lda);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[4];
+                const int k = kt + ak + 8 * h;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int m = m0 + am + i;
+                    bool ok = m < Mi && k < kend;
+                    if (a_low) ok = ok && k <= m;
+                    if (a_up) ok = ok && k >= m;
+                    float x = ok ? A[m + (int64_t)k * lda] : 0.f;
+                    if (a_unit && k == m) x = 1.f;
+                    v[i] = x;
+                }
+                ra[h] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        if (fast && n_full) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                rb[h] = *reinterpret_cast<const float4 *>(B + (kt + bk) + (int64_t)(n0 + bn + 64 * h) * ldb);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v[4];
+                const int nn = n0 + bn + 64 * h;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = kt + bk + i;
+                    bool ok = nn < Ni && k < kend;
+                    if (b_low) ok = ok && k >= nn;
+                    if (b_up) ok = ok && k <= nn;
+                    float x = ok ? B[k + (int64_t)nn * ldb] : 0.f;
+                    if (b_unit && k == nn) x = 1.f;
+                    v[i] = x;
+                }
+                rb[h] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) *reinterpret_cast<float4 *>(&As[buf][ak + 8 * h][am]) = ra[h];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            Bs[buf][bk + 0][bn + 64 * h] = rb[h].x;
+            Bs[buf][bk + 1][bn + 64 * h] = rb[h].y;
+            Bs[buf][bk + 2][bn + 64 * h] = rb[h].z;
+            Bs[buf][bk + 3][bn + 64 * h] = rb[h].w;
+        }
+    };
+    // compute: thread (ty, tx) owns rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, likewise columns
+    const int tx = tid % 16, ty = tid / 16;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    int buf = 0;
+    if (kbeg < kend) {
+        gload(kbeg);
+        sstore(0);
+        __syncthreads();
+    }
+    for (int kt = kbeg; kt < kend; kt += VBK) {
+        const bool more = kt + VBK < kend;
+        if (more) gload(kt + VBK);
+#pragma unroll
+        for (int kk = 0; kk < VBK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            const float fa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float fb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(fa[i], fb[j], acc[i][j]);
+        }
+        if (more) {
+            sstore(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (gm >= Mi) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (gn >= Ni) continue;
+            if (c_low && gn > gm) continue;
+            if (c_up && gm > gn) continue;
+            float *c = C + gm + (int64_t)gn * ldc;
+            if ((cmask == OP_LOWER_UNIT || cmask == OP_UPPER_UNIT) && gm == gn) {
+                if (ksplit == 1) *c = 0.f;
+                continue;
+            }
+            if (ksplit > 1) atomicAdd(c, alpha * acc[i][j]);
+            else *c = beta == 0.f ? alpha * acc[i][j] : fmaf(alpha, acc[i][j], beta * *c);
+        }
+    }
+}
+
 // Zeroes the part of C (M x N per matrix) that a product with output mask cmask writes.
 template <typename T>
 __global__ void zero_masked_kernel(T *C, int64_t M, int64_t N, int64_t ldc, int cmask, int64_t sc, int64_t nb1,
@@ -258,6 +435,14 @@ cudaError_t launch_f64(const Ctx &c, const GemmArgs &g) {
     return launch_g<double, 32, 32, 16, 2, 2>(c, g, ksplit);
 }
 
+// 16-byte groups of both operands: base pointers, leading dimensions and batch strides
+// multiples of 4 FP32 elements.
+bool vec_aligned(const GemmArgs &g) {
+    auto ok = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    return ok(g.a) && ok(g.b) && g.lda % 4 == 0 && g.ldb % 4 == 0 && g.sa % 4 == 0 && g.sb % 4 == 0 &&
+           g.sa2 % 4 == 0 && g.sb2 % 4 == 0;
+}
+
 }  // namespace
 
 double gemm_flops(const GemmArgs &g) {
@@ -289,6 +474,20 @@ cudaError_t gemm_simt(const Ctx &c, tri_dtype dt, const GemmArgs &g, const char 
         const int64_t want = (2 * (int64_t)c.sm_count + tiles - 1) / tiles;
         const int64_t most = std::max<int64_t>(1, g.k / 128);   // at least 128 of k per slice
         ksplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, most, 64, 65535 / mats}));
+    }
+    if (big && !g.ta && !g.tb && vec_aligned(g)) {
+        if (ksplit > 1) {
+            if (g.n > 65535) return cudaErrorInvalidValue;
+            dim3 zg((unsigned)((g.m + 255) / 256), (unsigned)g.n, (unsigned)mats);
+            zero_masked_kernel<float><<<zg, 256, 0, c.stream>>>((float *)g.c, g.m, g.n, g.ldc, g.cmask, g.sc, g.batch,
+                                                                g.sc2);
+        }
+        dim3 grid((unsigned)((g.n + VBN - 1) / VBN), (unsigned)((g.m + VBM - 1) / VBM), (unsigned)(mats * ksplit));
+        gemm_simt_vec_kernel<<<grid, VNT, 0, c.stream>>>(g.m, g.n, g.k, (float)g.alpha, (const float *)g.a, g.lda,
+                                                         g.akind, (const float *)g.b, g.ldb, g.bkind, (float)g.beta,
+                                                         (float *)g.c, g.ldc, g.cmask, g.sa, g.sb, g.sc, g.batch,
+                                                         g.sa2, g.sb2, g.sc2, ksplit);
+        return cudaGetLastError();
     }
     if (big) return launch_g<float, 128, 128, 8, 8, 8>(c, g, ksplit);
     return launch_g<float, 64, 64, 16, 4, 4>(c, g, ksplit);

@@ -18,6 +18,7 @@ struct Ctx {
     int device;
     float tau;         // growth limit of the FP64 fallback for ill-conditioned diagonal
                        // blocks (tri_set_growth_limit; <= 0 disables)
+    int recipe;        // TRI_F32_MIXED recipe of the triangular path (tri_set_mixed_recipe)
 };
 
 // Lower-orientation view of a column-major matrix.  For an upper-triangular matrix U

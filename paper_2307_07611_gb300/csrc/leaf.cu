@@ -129,8 +129,17 @@ __global__ void __launch_bounds__(NT) leaf_kernel(T *__restrict__ a, int64_t lda
 #pragma unroll
             for (int r = 0; r < RPT; ++r)
                 if (ig + r * G < nb && j < nb) xmax = fmaxf(xmax, fabsf(acc[r]));
-            atomicMax(&s_xmax, __float_as_uint(xmax));   // non-negative: bit order = value order
-            atomicMax(&s_tmax, __float_as_uint(tmax));
+            // one shared-memory atomic per warp (non-negative floats order like their bits)
+            float v = xmax, w = tmax;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                w = fmaxf(w, __shfl_xor_sync(0xffffffffu, w, o));
+            }
+            if ((tid & 31) == 0) {
+                atomicMax(&s_xmax, __float_as_uint(v));
+                atomicMax(&s_tmax, __float_as_uint(w));
+            }
             __syncthreads();
             const float growth = __uint_as_float(s_xmax) * __uint_as_float(s_tmax);
             if (!(growth <= tau)) {   // uniform over the CTA

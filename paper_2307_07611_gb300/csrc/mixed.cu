@@ -16,6 +16,9 @@
 //        X += X R          1 term: R is as small as the forward residual (~3e-8
 //                          normwise at n = 8192), so the BF16 error 2^-8 |X R| of the
 //                          update adds ~1e-10, far below FP32 rounding
+// Direct recipe (tri_set_mixed_recipe(TRI_RECIPE_DIRECT)): the level products of step 4
+// take all six terms with FP32 promotion every 64 k (FP32-class products, W with its lo
+// plane) and step 5 is left out.
 // Steps 4 and 5 run either as one persistent tensor-core launch per product (default)
 // or as a single launch that follows the data dependencies tile by tile (tc_graph.cu,
 // TRI_MIXED_SCHEDULE=graph).  Tile lists and schedules depend on n only and are built
@@ -84,7 +87,7 @@ struct Layout {
     size_t off_t, off_x, off_r, off_w, off_f, off_g, total;
 };
 
-// Workspace: T planes (3), X planes (3), R plane, W planes (2; single matrix: at the
+// Workspace: T planes (3), X planes (3), R plane, W planes (3; single matrix: at the
 // positions of the B blocks of T; batch: the compact h x P*h level layout), each a group of
 // `batch` planes, then the ready counters of the single-launch schedule, then one growth
 // flag per diagonal block of every matrix.
@@ -98,14 +101,14 @@ Layout layout(int64_t n, int64_t batch = 1) {
     L.off_x = L.off_t + 3 * g;
     L.off_r = L.off_x + 3 * g;
     L.off_w = L.off_r + g;
-    L.off_f = L.off_w + 2 * g;
+    L.off_f = L.off_w + 3 * g;
     L.off_g = L.off_f + al256(tc::graph_flag_bytes(n));
     L.total = L.off_g + al256((size_t)((n + kDiag - 1) / kDiag) * (size_t)batch * sizeof(int));
     return L;
 }
 
 int64_t chunk_matrices(int64_t n, int64_t batch) {
-    const size_t per = 9 * layout(n).plane;
+    const size_t per = 10 * layout(n).plane;
     return std::max<int64_t>(1, std::min<int64_t>(batch, (int64_t)(kChunkBytes / per)));
 }
 
@@ -163,13 +166,16 @@ bool use_graph_schedule() {
 }
 
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int64_t, int64_t>, Plan> g_plans;
+std::map<std::tuple<int, int64_t, int64_t, int>, Plan> g_plans;
 
 // Tile lists of every product for `batch` matrices of order n (each product's tiles of
-// all matrices in one longest-first schedule).
-tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **out) {
+// all matrices in one longest-first schedule).  recipe TRI_RECIPE_DIRECT: the level
+// products take six terms (longest-first costs follow) and there is no Newton-Schulz step.
+tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recipe, Plan **out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto key = std::make_tuple(dev, n, batch);
+    const bool direct = recipe == TRI_RECIPE_DIRECT;
+    const int lterms = direct ? 6 : 3;
+    auto key = std::make_tuple(dev, n, batch, recipe);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {
         *out = &it->second;
@@ -204,20 +210,20 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **ou
         double fl = 0.0;
         for (int64_t q = 0; q < P; ++q) {
             const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
-            fl += 3.0 * (double)hc * h * (h + 1);
+            fl += lterms * (double)hc * h * (h + 1);
             for (int64_t tn = 0; tn < h / bn; ++tn)
                 for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm)
                     v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * bn),
                                          (int)(tn * bn / tc::BK), (int)(h / tc::BK),
                                          (int)(tm * tc::BM), (int)(q * h + tn * bn)});
         }
-        add(&p.w, nullptr, from, fl, 3, bn);
+        add(&p.w, nullptr, from, fl, lterms, bn);
         // X21 = -X_C W
         from = v.size();
         fl = 0.0;
         for (int64_t q = 0; q < P; ++q) {
             const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
-            fl += 3.0 * (double)h * hc * (hc + 1);
+            fl += lterms * (double)h * hc * (hc + 1);
             for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
                 const int64_t kend = std::min((tm + 1) * tc::BM, hc);
                 for (int64_t tn = 0; tn < h / bn; ++tn)
@@ -226,11 +232,11 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, Plan **ou
                                          (int)(a0 + tn * bn)});
             }
         }
-        add(&p.x21, nullptr, from, fl, 3, bn);
+        add(&p.x21, nullptr, from, fl, lterms, bn);
     }
     // Newton-Schulz: lower x lower products over the whole matrix.
     const double lower_prod = (double)n * (n + 1) * (n + 2) / 3.0;   // 2 * sum_{i>=j} (i-j+1)
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < (direct ? 0 : 2); ++pass) {
         const size_t from = v.size();
         for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
             const int64_t kend = std::min((tm + 1) * tc::BM, n);
@@ -290,7 +296,7 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     uint8_t *base = (uint8_t *)ws;
     const size_t g = L.plane * (size_t)batch;   // bytes of one plane group
     const int64_t ps = (int64_t)(L.plane / 2);  // elements between the planes of consecutive matrices
-    __nv_bfloat16 *T[3], *X[3], *R[1], *W[2];
+    __nv_bfloat16 *T[3], *X[3], *R[1], *W[3];
     for (int i = 0; i < 3; ++i) {
         T[i] = (__nv_bfloat16 *)(base + L.off_t + i * g);
         X[i] = (__nv_bfloat16 *)(base + L.off_x + i * g);
@@ -298,12 +304,14 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     R[0] = (__nv_bfloat16 *)(base + L.off_r);
     W[0] = (__nv_bfloat16 *)(base + L.off_w);
     W[1] = (__nv_bfloat16 *)(base + L.off_w + g);
+    W[2] = (__nv_bfloat16 *)(base + L.off_w + 2 * g);
 
-    const bool graph = batch == 1 && use_graph_schedule();
+    const bool direct = c.recipe == TRI_RECIPE_DIRECT;
+    const bool graph = batch == 1 && !direct && use_graph_schedule();
     const tc::GraphPlan *gplan = nullptr;
     Plan *plan = nullptr;
     tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan)
-                          : build_plan(c.device, c.sm_count, n, batch, &plan);
+                          : build_plan(c.device, c.sm_count, n, batch, c.recipe, &plan);
     if (st != TRI_OK) return st;
 
     // 1. T planes of the off-diagonal part (side stream), concurrently with
@@ -315,16 +323,18 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     if (!side_stream(c.device, &ss)) return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->fork, c.stream) != cudaSuccess || cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
+    // The diagonal-block kernel goes first: each of its CTAs needs a whole SM's shared
+    // memory, so queued behind the split kernel's CTAs it would wait for SMs to drain (the
+    // split then fills the SMs it leaves free).
+    int *gflags = (int *)(base + L.off_g);   // growth flags (the single-launch schedule takes no fallback)
+    const float tau = graph ? 0.f : c.tau;
+    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2], batch, stride, ps,
+                           index0, tau, tau > 0.f ? gflags : nullptr) != cudaSuccess)
+        return TRI_ERR_CUDA;
     Ctx cs = c;
     cs.stream = ss->s;
     if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps) !=
         cudaSuccess)
-        return TRI_ERR_CUDA;
-    // growth flags of the diagonal blocks (the single-launch schedule takes no fallback)
-    int *gflags = (int *)(base + L.off_g);
-    const float tau = graph ? 0.f : c.tau;
-    if (launch_diag_blocks(c, trans, unit, n, a, lda, X[0], X[1], X[2], L.ldp, T[0], T[1], T[2], batch, stride, ps,
-                           index0, tau, tau > 0.f ? gflags : nullptr) != cudaSuccess)
         return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
@@ -346,27 +356,31 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     const tc::Plane tp[3] = {pl(T[0], n, n, L.ldp), pl(T[1], n, n, L.ldp), pl(T[2], n, n, L.ldp)};
     const tc::Plane xp[3] = {pl(X[0], n, n, L.ldp), pl(X[1], n, n, L.ldp), pl(X[2], n, n, L.ldp)};
     const tc::Terms three{3, {0, 0, 1}, {0, 1, 0}};
-    // 4. tensor-core levels
+    const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
+    // 4. tensor-core levels (direct recipe: six promoted terms, W with its lo plane)
+    const int mw = direct ? tc::MODE_W6 : tc::MODE_W, mx = direct ? tc::MODE_X216 : tc::MODE_X21;
+    const tc::Terms &lt = direct ? six : three;
+    const int nw = direct ? 3 : 2;
     int lvl = 0;
     for (int64_t h = kDiag; h < n; h *= 2, ++lvl) {
         const int64_t P = level_pairs(n, h);
-        const tc::Plane wp[2] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h)};
-        tc::Epi ew{nullptr, 0, W[0], W[1], nullptr, h, h, P * h};
+        const tc::Plane wp[3] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h), pl(W[2], h, P * h, h)};
+        tc::Epi ew{nullptr, 0, W[0], W[1], direct ? W[2] : nullptr, h, h, P * h};
         ew.os = ps;
         const Launch &lw = plan->w[lvl];
-        if (tc::launch_tc(c, tc::MODE_W, trans, unit, tp, 3, xp, 3, three, plan->d_tiles + lw.first,
-                          plan->d_off + lw.off_first, lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn) != cudaSuccess)
+        if (tc::launch_tc(c, mw, trans, unit, tp, 3, xp, 3, lt, plan->d_tiles + lw.first, plan->d_off + lw.off_first,
+                          lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn) != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         ex.xs = stride;
         ex.os = ps;
         const Launch &lx = plan->x21[lvl];
-        if (tc::launch_tc(c, tc::MODE_X21, trans, unit, xp, 3, wp, 2, three, plan->d_tiles + lx.first,
-                          plan->d_off + lx.off_first, lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn) != cudaSuccess)
+        if (tc::launch_tc(c, mx, trans, unit, xp, 3, wp, nw, lt, plan->d_tiles + lx.first, plan->d_off + lx.off_first,
+                          lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
+    if (direct) return TRI_OK;
     // 5. Newton-Schulz: R = I - T X, then X += X R
-    const tc::Terms six{6, {0, 0, 1, 0, 1, 2}, {0, 1, 0, 2, 1, 0}};
     tc::Epi er{nullptr, 0, R[0], nullptr, nullptr, L.ldp, n, n};
     er.os = ps;
     if (tau > 0.f) {

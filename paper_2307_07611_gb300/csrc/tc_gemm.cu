@@ -57,7 +57,9 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
                                               const uint32_t (&r)[NC], bool zero = false) {
     if (gm >= ep.mlim) return;
     const int64_t left = ep.nlim - gn0;
-    if (MODE == MODE_W || MODE == MODE_X21 || MODE == MODE_RES) {
+    // the six-term level products store exactly like their three-term forms
+    constexpr bool W = MODE == MODE_W || MODE == MODE_W6, X21 = MODE == MODE_X21 || MODE == MODE_X216;
+    if (W || X21 || MODE == MODE_RES) {
         int64_t off = ob + gm + gn0 * ep.ldo;
         int64_t xo = xb + vidx<TRANS>(gm, gn0, ep.ldx);
         const int64_t xstep = TRANS ? 1 : ep.ldx;
@@ -66,7 +68,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
             if (j < left) {
                 const float acc = __uint_as_float(r[j]);
                 float v = acc;
-                if (MODE == MODE_X21) {
+                if (X21) {
                     v = -acc;
                     ep.x[xo] = v;
                 } else if (MODE == MODE_RES) {
@@ -78,7 +80,7 @@ __device__ __forceinline__ void epilogue_cols(const Epi &ep, int64_t xb, int64_t
                 const __nv_bfloat16 m = __float2bfloat16_rn(r1);
                 ep.o0[off] = h;
                 if (MODE != MODE_RES || ep.o1) ep.o1[off] = m;
-                if (MODE == MODE_X21) ep.o2[off] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+                if (X21 || MODE == MODE_W6) ep.o2[off] = __float2bfloat16_rn(r1 - __bfloat162float(m));
             }
             off += ep.ldo;
             xo += xstep;
@@ -165,7 +167,8 @@ struct Cfg {
     int promote;
 };
 __host__ __device__ constexpr Cfg cfg_for(int mode) {
-    return (mode == MODE_RES || mode == MODE_GENP) ? Cfg{32, true, 1} : Cfg{64, false, 0};
+    return (mode == MODE_RES || mode == MODE_GENP || mode == MODE_W6 || mode == MODE_X216) ? Cfg{32, true, 1}
+                                                                                         : Cfg{64, false, 0};
 }
 
 constexpr int STAGE_BUDGET = 216 * 1024;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe pipe,
                const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
                int *gtimeout) {
-    constexpr bool PROMOTE = (MODE == MODE_RES || MODE == MODE_GENP);
+    constexpr bool PROMOTE = (MODE == MODE_RES || MODE == MODE_GENP || MODE == MODE_W6 || MODE == MODE_X216);
     constexpr Cfg CF = cfg_for(MODE);
     constexpr int KS = CF.ks;
     constexpr int A_TILE = BM * KS * 2, B_TILE = BNT * KS * 2;
@@ -585,7 +588,8 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     if (ctas <= 0) return cudaSuccess;
     if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
     // narrow tiles are built for the level products only
-    if (bn != BN && !((bn == 128 || bn == 64) && (mode == MODE_W || mode == MODE_X21))) return cudaErrorInvalidValue;
+    const bool level = mode == MODE_W || mode == MODE_X21 || mode == MODE_W6 || mode == MODE_X216;
+    if (bn != BN && !((bn == 128 || bn == 64) && level)) return cudaErrorInvalidValue;
     Maps maps;
     memset(&maps, 0, sizeof(maps));
     const Cfg cf = cfg_for(mode);
@@ -628,6 +632,8 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     switch (mode) {
         TRI_TC_CASE_LEVEL(MODE_W)
         TRI_TC_CASE_LEVEL(MODE_X21)
+        TRI_TC_CASE_LEVEL(MODE_W6)
+        TRI_TC_CASE_LEVEL(MODE_X216)
         TRI_TC_CASE(MODE_RES)
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:

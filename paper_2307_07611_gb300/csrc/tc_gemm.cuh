@@ -55,6 +55,8 @@ enum Mode {
     MODE_GEN = 5,    // x <- alpha acc + beta x, column-major, masked        (general products)
     MODE_GENP = 6,   // MODE_GEN with fused stages and FP32 promotion of the partial sums
                      // every 64 k (the six-term products that must reach ~2^-24)
+    MODE_W6 = 7,     // MODE_W with six promoted terms; o0/o1/o2 <- hi/mid/lo  (direct recipe)
+    MODE_X216 = 8,   // MODE_X21 with six promoted terms                       (direct recipe)
 };
 
 // A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld
@@ -82,7 +84,7 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
 // tiles d_tiles[d_off[b] .. d_off[b+1]).  aplanes/bplanes: up to 3 planes each, indexed
 // by `terms`.
 // bn: columns of the output tiles the list was built with: BN, or 128 / 64 for the level
-// products (MODE_W, MODE_X21).
+// products (MODE_W, MODE_X21, MODE_W6, MODE_X216).
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
                       int na, const Plane *bplanes, int nb, const Terms &terms,
                       const Tile *d_tiles, const int *d_off, int ctas, const Epi &epi,

@@ -18,6 +18,20 @@ namespace triinv {
 constexpr int TP = 33;   // tile row pitch (elements)
 constexpr int TE = 32 * TP;
 
+// Maximum of v over the warp's lanes (every lane gets it).
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// *m = max(*m, v) over a CTA for non-negative v (float bits order like the values): one
+// shared-memory atomic per warp (all lanes of the warp must take part).
+__device__ __forceinline__ void block_max_nonneg(unsigned *m, float v) {
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) atomicMax(m, __float_as_uint(v));
+}
+
 template <typename T>
 __device__ __forceinline__ T *tile_ptr(T *tiles, int I, int J) {
     return tiles + (size_t)(I * (I + 1) / 2 + J) * TE;
@@ -103,16 +117,21 @@ __device__ __forceinline__ int invert_tiles(T *tiles, T *wt, int nt, int n) {
         // W_q(Iw, Jw) = sum_{K >= Jw} B(c0 + Iw, a0 + K) X(a0 + K, a0 + Jw)
         int jobs = 0;
         for (int q = 0; q < pairs; ++q) jobs += min(ht, nt - (2 * q * ht + ht)) * ht;
+        // Job order within a pair is column-major (Jw outer): a W tile's length ht - Jw
+        // depends on its column, and warps w, w + 4, ... share one SM sub-partition, so
+        // consecutive warps take tiles of different lengths.  The tile is stored at
+        // base + Iw * ht + Jw, where the X21 phase reads it.
         for (int jb = warp; jb < jobs; jb += nwarps) {
-            int q = 0, rest = jb;
+            int q = 0, rest = jb, base = 0, hc = 0;
             for (;;) {
-                const int hc = min(ht, nt - (2 * q * ht + ht));
+                hc = min(ht, nt - (2 * q * ht + ht));
                 if (rest < hc * ht) break;
                 rest -= hc * ht;
+                base += hc * ht;
                 ++q;
             }
             const int a0 = 2 * q * ht, c0 = a0 + ht;
-            const int Iw = rest / ht, Jw = rest % ht;
+            const int Jw = rest / hc, Iw = rest % hc;
             T acc[4][8];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -120,7 +139,7 @@ __device__ __forceinline__ int invert_tiles(T *tiles, T *wt, int nt, int n) {
                 for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
             for (int K = Jw; K < ht; ++K)
                 warp_mma32(tile_ptr(tiles, c0 + Iw, a0 + K), tile_ptr(tiles, a0 + K, a0 + Jw), acc, lane);
-            warp_store32(wt + (size_t)jb * TE, acc, lane, T(1));
+            warp_store32(wt + (size_t)(base + Iw * ht + Jw) * TE, acc, lane, T(1));
         }
         __syncthreads();
         // B(c0 + Iw, a0 + Jw) <- -sum_{K <= Iw} X_C(c0 + Iw, c0 + K) W_q(K, Jw)
@@ -182,15 +201,16 @@ __device__ __forceinline__ void invert_tiles_multi(T *const (&tiles)[NM], T *con
         for (int x = warp; x < NM * jobs; x += nwarps) {
             const int mtx = x / jobs, jb = x % jobs;
             T *tl = pick(tiles, mtx);
-            int q = 0, rest = jb;
+            int q = 0, rest = jb, base = 0, hc = 0;
             for (;;) {
-                const int hc = min(ht, nt - (2 * q * ht + ht));
+                hc = min(ht, nt - (2 * q * ht + ht));
                 if (rest < hc * ht) break;
                 rest -= hc * ht;
+                base += hc * ht;
                 ++q;
             }
             const int a0 = 2 * q * ht, c0 = a0 + ht;
-            const int Iw = rest / ht, Jw = rest % ht;
+            const int Jw = rest / hc, Iw = rest % hc;   // column-major, as in invert_tiles
             T acc[4][8];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -198,7 +218,7 @@ __device__ __forceinline__ void invert_tiles_multi(T *const (&tiles)[NM], T *con
                 for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
             for (int K = Jw; K < ht; ++K)
                 warp_mma32(tile_ptr(tl, c0 + Iw, a0 + K), tile_ptr(tl, a0 + K, a0 + Jw), acc, lane);
-            warp_store32(pick(wt, mtx) + (size_t)jb * TE, acc, lane, T(1));
+            warp_store32(pick(wt, mtx) + (size_t)(base + Iw * ht + Jw) * TE, acc, lane, T(1));
         }
         __syncthreads();
         for (int x = warp; x < NM * jobs; x += nwarps) {

@@ -81,6 +81,8 @@ def _declare(lib):
         "tri_mixed_schedule_stats": ([i64, i32, ctypes.POINTER(ctypes.c_double), i32], i32),
         "tri_batched_partition": ([i64, ctypes.POINTER(i64), i32, ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_double)], i32),
+        "tri_set_mixed_recipe": ([i32], i32),
+        "tri_mixed_recipe": ([], i32),
         "tri_set_growth_limit": ([ctypes.c_double], i32),
         "tri_growth_limit": ([], ctypes.c_double),
         "tri_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -327,6 +329,18 @@ def tri_get_info(stream=0):
     idx = ctypes.c_int64(-1)
     st = load().tri_get_info(stream or None, ctypes.byref(idx))
     return st, idx.value
+
+
+TRI_RECIPE_NEWTON_SCHULZ = 0
+TRI_RECIPE_DIRECT = 1
+
+
+def tri_set_mixed_recipe(recipe: int) -> int:
+    return load().tri_set_mixed_recipe(int(recipe))
+
+
+def tri_mixed_recipe() -> int:
+    return int(load().tri_mixed_recipe())
 
 
 def tri_set_growth_limit(tau: float) -> int:
