@@ -267,8 +267,28 @@ TRI_API tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, 
                                            tri_batched_plan **out);
 TRI_API tri_status tri_batched_exec(tri_batched_plan *plan, void *stream);
 TRI_API tri_status tri_batched_plan_destroy(tri_batched_plan *plan);
-/* Thread count the autotuner chose for this plan (diagnostic). */
+/* Thread count the autotuner chose for the plan's largest size class (diagnostic). */
 TRI_API int tri_batched_plan_threads(const tri_batched_plan *plan);
+
+/* The plan's CTA shape per size class (diagnostic): the blocks are split into classes,
+ * each its own persistent launch over a largest-first queue, replayed in order:
+ *   cls 0: 129..256 rows (FP32) -- 8 x 8 tiles of 32, one CTA per SM, 256 or 512 threads;
+ *   cls 1: 33..128 rows -- 4 x 4 tiles, several CTAs per SM, 128 or 256 threads;
+ *   cls 2: up to 32 rows -- one tile, 32 or 64 threads, many CTAs per SM.
+ * The autotuner times each candidate thread count (with the CTAs that fit beside it) on a
+ * scratch copy of the class's sizes when the plan is created and keeps the fastest.
+ * blocks / threads / ctas (each may be NULL): the class's block count, threads per CTA
+ * and persistent CTAs.  Errors: TRI_ERR_ARG (null plan, cls outside 0..2). */
+TRI_API tri_status tri_batched_plan_shape(const tri_batched_plan *plan, int cls, int *blocks, int *threads,
+                                          int *ctas);
+
+/* The autotuner's choices of this process (keyed by GPU model and SM count, dtype, size
+ * class and the histogram of the class's sizes) written to / read from a JSON file, so a
+ * later process skips the timing runs for batches it has seen.  Load merges into the
+ * process's cache (loaded: entries read; may be NULL).  Errors: TRI_ERR_ARG (null path,
+ * file not writable / readable, malformed entry). */
+TRI_API tri_status tri_tune_cache_save(const char *path);
+TRI_API tri_status tri_tune_cache_load(const char *path, int *loaded);
 
 /* Growth limit of an FP32 plan: an FP64 leaf only for ill-conditioned blocks.  After a
  * block's FP32 inverse, if max|X| * max|T| > tau (a lower bound of its condition number

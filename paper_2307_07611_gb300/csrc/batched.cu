@@ -281,22 +281,25 @@ __device__ __forceinline__ void invert_block(const BDesc &d, T *tiles, T *wt, lo
             redo = !(growth <= tau);
         }
         if (redo_flag && tid == 0) *redo_flag = redo ? 1 : 0;
-        if (redo && n <= 128) {
-            // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
-            // the shared memory of the FP32 block
-            double *dt = reinterpret_cast<double *>(tiles);
-            invert_block<double, TRANS, UNIT, 4, NT, float>(d, dt, dt + (size_t)BLimits<4>::kTiles * TE, info,
-                                                            row0, nullptr, nullptr, nullptr, 0, ntot, nullptr,
-                                                            nullptr, nullptr, info_as, 0.f);
-            if (p0 != nullptr) {
-                load_tiles<float, TRANS, UNIT, NT, S>(d, tiles);
-                __syncthreads();
-                write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
+        if constexpr (MAXT >= 8) {
+            if (redo && n <= 128) {
+                // FP64 again from the unchanged source; the FP64 tiles of a 128-block fit in
+                // the shared memory of the FP32 block of 256
+                double *dt = reinterpret_cast<double *>(tiles);
+                invert_block<double, TRANS, UNIT, 4, NT, float>(d, dt, dt + (size_t)BLimits<4>::kTiles * TE, info,
+                                                                row0, nullptr, nullptr, nullptr, 0, ntot, nullptr,
+                                                                nullptr, nullptr, info_as, 0.f);
+                if (p0 != nullptr) {
+                    load_tiles<float, TRANS, UNIT, NT, S>(d, tiles);
+                    __syncthreads();
+                    write_planes<T, NT>(tiles, nt, n, row0, ntot, p0, p1, p2, ldp);
+                }
+                return;
             }
-            return;
         }
         if (redo) {
-            // FP64 column recurrence from the unchanged source, stored directly
+            // FP64 column recurrence from the unchanged source, stored directly (its staging,
+            // n(n+1)/2 floats and 256 doubles per warp, fits the FP32 tiles of every class)
             redo_columns_fp64<TRANS, UNIT, NT>(d, reinterpret_cast<uint8_t *>(tiles));
             if (p0 != nullptr) {
                 load_tiles<float, TRANS, UNIT, NT, S>(d, tiles);
@@ -393,9 +396,16 @@ __global__ void __launch_bounds__(512, 1) diag_blocks_kernel(float *a, long long
                                              flags ? flags + mb * gridDim.x + blockIdx.x : nullptr);
 }
 
-template <typename T, int MAXT>
+// Dynamic shared memory of a class kernel: its tiles and the top level's W, or for FP32
+// the staging of the FP64 column recurrence (n(n+1)/2 floats, 16-byte aligned, and 256
+// doubles per warp) if that is larger.
+template <typename T, int MAXT, int NT = 512>
 size_t smem_bytes() {
-    return (size_t)(BLimits<MAXT>::kTiles + BLimits<MAXT>::kWTiles) * TE * sizeof(T);
+    const size_t tiles = (size_t)(BLimits<MAXT>::kTiles + BLimits<MAXT>::kWTiles) * TE * sizeof(T);
+    if (!std::is_same<T, float>::value) return tiles;
+    const size_t nmax = 32 * (size_t)MAXT;
+    const size_t redo = (nmax * (nmax + 1) / 2 * 4 + 15) / 16 * 16 + (size_t)(NT / 32) * 256 * 8;
+    return std::max(tiles, redo);
 }
 
 using KernFn = void (*)(const BDesc *, int, int *, long long *, const float *);
@@ -406,13 +416,35 @@ KernFn pick3(bool trans, bool unit) {
     return unit ? batched_kernel<T, false, true, MAXT, NT> : batched_kernel<T, false, false, MAXT, NT>;
 }
 
-// Kernel for a precision, orientation, diagonal kind and thread count (256 or 512).
-KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int threads, size_t *smem) {
-    if (dt == TRI_F64) {
-        *smem = smem_bytes<double, 4>();
-        return threads == 256 ? pick3<double, 4, 256>(trans, unit) : pick3<double, 4, 512>(trans, unit);
+// Size classes of a batch, each its own persistent launch with its own CTA shape:
+//   class 0  129..256 rows (FP32): 8 x 8 tiles, 220 KB of shared memory, one CTA per SM;
+//   class 1  33..128 rows: 4 x 4 tiles (59 KB FP32, 118 KB FP64), several CTAs per SM;
+//   class 2  up to 32 rows: one tile, one warp per CTA, many CTAs per SM.
+// Candidate thread counts per class (the autotuner times them); 0 ends a list.
+constexpr int kClasses = 3;
+constexpr int kCandidates[kClasses][3] = {{512, 256, 0}, {128, 256, 0}, {32, 64, 0}};
+
+int size_class(int64_t n) { return n > 128 ? 0 : (n > 32 ? 1 : 2); }
+
+// Kernel for a precision, orientation, diagonal kind, size class and thread count.
+KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int cls, int threads, size_t *smem) {
+    if (cls == 2) {
+        if (dt == TRI_F64) {
+            *smem = smem_bytes<double, 1>();
+            return threads == 64 ? pick3<double, 1, 64>(trans, unit) : pick3<double, 1, 32>(trans, unit);
+        }
+        *smem = threads == 64 ? smem_bytes<float, 1, 64>() : smem_bytes<float, 1, 32>();
+        return threads == 64 ? pick3<float, 1, 64>(trans, unit) : pick3<float, 1, 32>(trans, unit);
     }
-    *smem = smem_bytes<float, 8>();
+    if (cls == 1) {
+        if (dt == TRI_F64) {
+            *smem = smem_bytes<double, 4>();
+            return threads == 256 ? pick3<double, 4, 256>(trans, unit) : pick3<double, 4, 128>(trans, unit);
+        }
+        *smem = threads == 256 ? smem_bytes<float, 4, 256>() : smem_bytes<float, 4, 128>();
+        return threads == 256 ? pick3<float, 4, 256>(trans, unit) : pick3<float, 4, 128>(trans, unit);
+    }
+    *smem = threads == 256 ? smem_bytes<float, 8, 256>() : smem_bytes<float, 8, 512>();
     return threads == 256 ? pick3<float, 8, 256>(trans, unit) : pick3<float, 8, 512>(trans, unit);
 }
 
@@ -451,12 +483,13 @@ struct tri_batched_plan {
     int count = 0;
     tri_dtype dtype = TRI_F32;
     bool trans = false, unit = false;
-    triinv::BDesc *d_desc = nullptr;   // sorted, largest first
-    int *d_counter = nullptr;
+    triinv::BDesc *d_desc = nullptr;   // sorted, largest first: classes 0, 1, 2 in order
+    int *d_counter = nullptr;          // one queue counter per size class
     float *d_tau = nullptr;            // growth limit of the FP64 fallback (device, FP32 plans)
-    int threads = 512;
-    int ctas = 0;
-    size_t smem = 0;
+    int first[3] = {0, 0, 0};          // first descriptor of each size class
+    int nclass[3] = {0, 0, 0};         // blocks of each size class
+    int threads[3] = {0, 0, 0};        // tuned threads per CTA of each class
+    int ctas[3] = {0, 0, 0};           // persistent CTAs of each class
     double flops = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -473,82 +506,121 @@ constexpr float kDefaultGrowthLimit = 1.0e4f;   // FP32 batches: max|X| max|T| b
 // before stream capture).
 cudaError_t allow_smem(tri_dtype dt, bool trans) {
     for (int u = 0; u < 2; ++u)
-        for (int th : {256, 512}) {
-            size_t smem = 0;
-            KernFn k = pick_kernel(dt, trans, u != 0, th, &smem);
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
+        for (int cls = 0; cls < kClasses; ++cls)
+            for (int i = 0; kCandidates[cls][i]; ++i) {
+                size_t smem = 0;
+                KernFn k = pick_kernel(dt, trans, u != 0, cls, kCandidates[cls][i], &smem);
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
-cudaError_t launch_plan_kernel(const tri_batched_plan *p, cudaStream_t s, long long *info, int threads) {
+// Persistent CTAs of a class: as many as fit on the device (occupancy of the kernel with
+// its shared memory), at most one per block.
+int class_ctas(const tri_batched_plan *p, int cls, int threads, int sm_count) {
     size_t smem = 0;
-    KernFn k = pick_kernel(p->dtype, p->trans, p->unit, threads, &smem);
-    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), s);
+    KernFn k = pick_kernel(p->dtype, p->trans, p->unit, cls, threads, &smem);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return std::max(1, std::min(p->nclass[cls], per_sm * sm_count));
+}
+
+// Resets the class's queue and launches its persistent kernel.
+cudaError_t launch_class(const tri_batched_plan *p, int cls, cudaStream_t s, long long *info, int threads,
+                         int ctas) {
+    if (p->nclass[cls] == 0) return cudaSuccess;
+    size_t smem = 0;
+    KernFn k = pick_kernel(p->dtype, p->trans, p->unit, cls, threads, &smem);
+    cudaError_t e = cudaMemsetAsync(p->d_counter + cls, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k<<<p->ctas, threads, smem, s>>>(p->d_desc, p->count, p->d_counter, info, p->d_tau);
+    k<<<ctas, threads, smem, s>>>(p->d_desc + p->first[cls], p->nclass[cls], p->d_counter + cls, info, p->d_tau);
     return cudaGetLastError();
 }
 
-// Autotuner: time each candidate thread count on a scratch copy of the batch shape
-// (identity blocks of the same sizes, so the caller's data is untouched) and keep the
-// fastest.  Results are cached per (device, size histogram) for the process.
+// ---- autotuner and its cache ---------------------------------------------------------
+// For each size class the tuner times every candidate thread count (and the CTA count
+// that fits with it) on a scratch copy of the class's block sizes (identity blocks, unit
+// diagonal, so the caller's data is untouched) and keeps the fastest.  Choices are cached
+// per (GPU model, SM count, dtype, class, histogram of the class's sizes in 16-row buckets)
+// for the process, and tri_tune_cache_save / tri_tune_cache_load keep them in a JSON file.
 std::mutex g_tune_mu;
 std::vector<std::pair<std::string, int>> g_tune_cache;
 
-int autotune(tri_batched_plan *p, const std::vector<int64_t> &sizes_sorted, const Ctx &c) {
-    std::string key = std::to_string(c.device) + ":" + std::to_string((int)p->dtype) + ":";
-    {
-        // histogram of sizes in 16-wide buckets
-        std::vector<int> h(33, 0);
-        for (int64_t s : sizes_sorted) h[std::min<int64_t>(32, s / 16)]++;
-        for (int v : h) key += std::to_string(v) + ",";
+std::string device_tag(int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
     }
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || ch == ' ') ch = '_';
+    return name + "/" + std::to_string(prop.multiProcessorCount);
+}
+
+std::string tune_key(const tri_batched_plan *p, int cls, const std::vector<int64_t> &sizes, int dev) {
+    std::string key = device_tag(dev) + ":" + std::to_string((int)p->dtype) + ":c" + std::to_string(cls) + ":";
+    std::vector<int> h(17, 0);
+    for (int64_t s : sizes) h[std::min<int64_t>(16, s / 16)]++;
+    for (int v : h) key += std::to_string(v) + ",";
+    return key;
+}
+
+int autotune_class(tri_batched_plan *p, int cls, const std::vector<int64_t> &sizes, const Ctx &c) {
+    const std::string key = tune_key(p, cls, sizes, c.device);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (auto &kv : g_tune_cache)
             if (kv.first == key) return kv.second;
     }
-    const char *env = getenv("TRI_BATCHED_THREADS");
-    if (env) return atoi(env) == 256 ? 256 : 512;
-    // scratch blocks (identity), same sizes, dense column-major
+    int best = kCandidates[cls][0];
+    if (const char *env = getenv("TRI_BATCHED_THREADS")) {   // forced choice (class 0 only)
+        if (cls == 0) return atoi(env) == 256 ? 256 : 512;
+    }
     size_t total = 0;
-    for (int64_t s : sizes_sorted) total += (size_t)s * s;
+    for (int64_t s : sizes) total += (size_t)s * s;
     const size_t es = p->dtype == TRI_F64 ? 8 : 4;
     void *scratch = nullptr;
     BDesc *d_scr = nullptr;
     long long *d_info = nullptr;
-    int best = 512;
-    if (cudaMalloc(&scratch, total * es) != cudaSuccess || cudaMalloc(&d_scr, sizeof(BDesc) * sizes_sorted.size()) != cudaSuccess ||
-        cudaMalloc(&d_info, sizeof(long long)) != cudaSuccess) {
+    int *d_cnt = nullptr;
+    if (cudaMalloc(&scratch, total * es) != cudaSuccess || cudaMalloc(&d_scr, sizeof(BDesc) * sizes.size()) != cudaSuccess ||
+        cudaMalloc(&d_info, sizeof(long long)) != cudaSuccess || cudaMalloc(&d_cnt, 3 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(scratch);
         cudaFree(d_scr);
         cudaFree(d_info);
+        cudaFree(d_cnt);
         return best;
     }
     cudaMemset(scratch, 0, total * es);
-    std::vector<BDesc> hd(sizes_sorted.size());
+    std::vector<BDesc> hd(sizes.size());
     size_t off = 0;
-    for (size_t i = 0; i < sizes_sorted.size(); ++i) {
-        hd[i] = BDesc{(uint8_t *)scratch + off * es, (long long)sizes_sorted[i], (int)sizes_sorted[i], (int)i};
-        off += (size_t)sizes_sorted[i] * sizes_sorted[i];
+    for (size_t i = 0; i < sizes.size(); ++i) {
+        hd[i] = BDesc{(uint8_t *)scratch + off * es, (long long)sizes[i], (int)sizes[i], (int)i};
+        off += (size_t)sizes[i] * sizes[i];
     }
     cudaMemcpy(d_scr, hd.data(), sizeof(BDesc) * hd.size(), cudaMemcpyHostToDevice);
     tri_batched_plan tmp = *p;
-    tmp.d_desc = d_scr;
+    tmp.d_desc = d_scr - p->first[cls];   // launch_class adds first[cls]
+    tmp.d_counter = d_cnt;
     tmp.unit = true;   // identity scratch: unit diagonal, no pivots to check
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
-    for (int th : {256, 512}) {
+    for (int i = 0; kCandidates[cls][i]; ++i) {
+        const int th = kCandidates[cls][i];
+        const int ctas = class_ctas(&tmp, cls, th, c.sm_count);
         float ms = 0.f;
         bool ok = true;
         for (int rep = 0; rep < 3 && ok; ++rep) {
             cudaEventRecord(e0, c.stream);
-            ok = launch_plan_kernel(&tmp, c.stream, d_info, th) == cudaSuccess;
+            ok = launch_class(&tmp, cls, c.stream, d_info, th, ctas) == cudaSuccess;
             cudaEventRecord(e1, c.stream);
             cudaEventSynchronize(e1);
             float t = 0.f;
@@ -566,6 +638,7 @@ int autotune(tri_batched_plan *p, const std::vector<int64_t> &sizes_sorted, cons
     cudaFree(scratch);
     cudaFree(d_scr);
     cudaFree(d_info);
+    cudaFree(d_cnt);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache.push_back({key, best});
     return best;
@@ -603,14 +676,20 @@ tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *co
         if (sizes[i] > 0) order.push_back(i);
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return sizes[a] > sizes[b]; });
     std::vector<BDesc> hd;
-    std::vector<int64_t> ss;
+    std::vector<int64_t> cls_sizes[kClasses];
     for (int64_t i : order) {
         hd.push_back(BDesc{ptrs[i], (long long)sizes[i], (int)sizes[i], (int)i});
-        ss.push_back(sizes[i]);
+        cls_sizes[size_class(sizes[i])].push_back(sizes[i]);
         p->flops += (double)sizes[i] * sizes[i] * sizes[i] / 3.0;
     }
     p->count = (int)hd.size();
-    if (cudaMalloc(&p->d_counter, sizeof(int)) != cudaSuccess || cudaMalloc(&p->d_tau, sizeof(float)) != cudaSuccess) {
+    for (int cl = 0, f = 0; cl < kClasses; ++cl) {   // sorted descending: classes are contiguous
+        p->first[cl] = f;
+        p->nclass[cl] = (int)cls_sizes[cl].size();
+        f += p->nclass[cl];
+    }
+    if (cudaMalloc(&p->d_counter, kClasses * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->d_tau, sizeof(float)) != cudaSuccess) {
         cudaFree(p->d_counter);
         delete p;
         cudaGetLastError();
@@ -628,21 +707,25 @@ tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *co
     if (p->count > 0) {
         if (cudaMalloc(&p->d_desc, sizeof(BDesc) * hd.size()) != cudaSuccess) {
             cudaFree(p->d_counter);
+            cudaFree(p->d_tau);
             delete p;
             cudaGetLastError();
             return TRI_ERR_NOMEM;
         }
         cudaMemcpy(p->d_desc, hd.data(), sizeof(BDesc) * hd.size(), cudaMemcpyHostToDevice);
     }
-    pick_kernel(p->dtype, p->trans, p->unit, 512, &p->smem);
     if (allow_smem(p->dtype, p->trans) != cudaSuccess) {
         cudaGetLastError();
         tri_batched_plan_destroy(p);
         return TRI_ERR_CUDA;
     }
-    p->ctas = std::max(1, std::min(c.sm_count, p->count));
-    p->threads = p->count > 0 ? autotune(p, ss, c) : 512;
-    // Capture {reset queue, persistent kernel} once; tri_batched_exec replays it.
+    for (int cl = 0; cl < kClasses; ++cl) {
+        if (p->nclass[cl] == 0) continue;
+        p->threads[cl] = autotune_class(p, cl, cls_sizes[cl], c);
+        p->ctas[cl] = class_ctas(p, cl, p->threads[cl], c.sm_count);
+    }
+    // Capture {reset queue, persistent kernel} per class, largest class first; replayed by
+    // tri_batched_exec.
     if (p->count > 0) {
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -650,7 +733,8 @@ tri_status tri_batched_plan_create(int64_t count, const int64_t *sizes, void *co
             return TRI_ERR_CUDA;
         }
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        ok = ok && launch_plan_kernel(p, cs, c.info, p->threads) == cudaSuccess;
+        for (int cl = 0; cl < kClasses && ok; ++cl)
+            ok = launch_class(p, cl, cs, c.info, p->threads[cl], p->ctas[cl]) == cudaSuccess;
         ok = (cudaStreamEndCapture(cs, &p->graph) == cudaSuccess) && ok;
         ok = ok && cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
         cudaStreamDestroy(cs);
@@ -693,7 +777,73 @@ tri_status tri_batched_plan_set_growth_limit(tri_batched_plan *plan, double tau)
     return cudaMemcpy(plan->d_tau, &t, sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess ? TRI_OK : TRI_ERR_CUDA;
 }
 
-int tri_batched_plan_threads(const tri_batched_plan *plan) { return plan ? plan->threads : 0; }
+int tri_batched_plan_threads(const tri_batched_plan *plan) {
+    if (!plan) return 0;
+    for (int cl = 0; cl < kClasses; ++cl)
+        if (plan->nclass[cl] > 0) return plan->threads[cl];
+    return 0;
+}
+
+tri_status tri_batched_plan_shape(const tri_batched_plan *plan, int cls, int *blocks, int *threads, int *ctas) {
+    if (!plan || cls < 0 || cls >= kClasses) return TRI_ERR_ARG;
+    if (blocks) *blocks = plan->nclass[cls];
+    if (threads) *threads = plan->threads[cls];
+    if (ctas) *ctas = plan->ctas[cls];
+    return TRI_OK;
+}
+
+tri_status tri_tune_cache_save(const char *path) {
+    if (!path) return TRI_ERR_ARG;
+    std::vector<std::pair<std::string, int>> v;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        v = g_tune_cache;
+    }
+    FILE *f = fopen(path, "w");
+    if (!f) return TRI_ERR_ARG;
+    fprintf(f, "{\"version\": 1, \"entries\": [");
+    for (size_t i = 0; i < v.size(); ++i)
+        fprintf(f, "%s\n  {\"key\": \"%s\", \"threads\": %d}", i ? "," : "", v[i].first.c_str(), v[i].second);
+    fprintf(f, "\n]}\n");
+    return fclose(f) == 0 ? TRI_OK : TRI_ERR_ARG;
+}
+
+tri_status tri_tune_cache_load(const char *path, int *loaded) {
+    if (loaded) *loaded = 0;
+    if (!path) return TRI_ERR_ARG;
+    FILE *f = fopen(path, "r");
+    if (!f) return TRI_ERR_ARG;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    fclose(f);
+    // entries of the form {"key": "...", "threads": N}, as written by tri_tune_cache_save
+    int count = 0;
+    size_t pos = 0;
+    while ((pos = text.find("\"key\": \"", pos)) != std::string::npos) {
+        pos += 8;
+        const size_t q = text.find('"', pos);
+        if (q == std::string::npos) return TRI_ERR_ARG;
+        const std::string key = text.substr(pos, q - pos);
+        const size_t t = text.find("\"threads\":", q);
+        if (t == std::string::npos) return TRI_ERR_ARG;
+        const int th = atoi(text.c_str() + t + 10);
+        if (th != 32 && th != 64 && th != 128 && th != 256 && th != 512) return TRI_ERR_ARG;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        bool found = false;
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) {
+                kv.second = th;
+                found = true;
+            }
+        if (!found) g_tune_cache.push_back({key, th});
+        ++count;
+        pos = t;
+    }
+    if (loaded) *loaded = count;
+    return TRI_OK;
+}
 
 tri_status tri_inv_batched(int64_t count, const int64_t *sizes, void *const *ptrs, tri_uplo uplo, tri_diag diag,
                            tri_dtype dtype, void *stream) {

@@ -62,6 +62,9 @@ def _declare(lib):
         "tri_batched_exec": ([vp, vp], i32),
         "tri_batched_plan_destroy": ([vp], i32),
         "tri_batched_plan_threads": ([vp], i32),
+        "tri_batched_plan_shape": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "tri_tune_cache_save": ([ctypes.c_char_p], i32),
+        "tri_tune_cache_load": ([ctypes.c_char_p, ctypes.POINTER(i32)], i32),
         "tri_batched_plan_set_growth_limit": ([vp, ctypes.c_double], i32),
         "tri_inv_batched": ([i64, ctypes.POINTER(i64), ctypes.POINTER(vp), i32, i32, i32, vp], i32),
         "gen_inv_workspace_size": ([i64, i32], sz),
@@ -225,6 +228,24 @@ def tri_batched_plan_destroy(plan) -> int:
 
 def tri_batched_plan_threads(plan) -> int:
     return load().tri_batched_plan_threads(plan)
+
+
+def tri_batched_plan_shape(plan, cls):
+    """(blocks, threads, ctas) of size class cls (0: 129..256 rows, 1: 33..128, 2: <= 32)."""
+    b, t, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    check(load().tri_batched_plan_shape(plan, int(cls), ctypes.byref(b), ctypes.byref(t), ctypes.byref(c)),
+          "tri_batched_plan_shape")
+    return b.value, t.value, c.value
+
+
+def tri_tune_cache_save(path: str) -> int:
+    return load().tri_tune_cache_save(path.encode())
+
+
+def tri_tune_cache_load(path: str):
+    n = ctypes.c_int(0)
+    st = load().tri_tune_cache_load(path.encode(), ctypes.byref(n))
+    return st, n.value
 
 
 def tri_batched_plan_set_growth_limit(plan, tau) -> int:

@@ -219,3 +219,17 @@ def test_brsi_argument_errors_need_no_gpu(libtri):
     assert need >= 4 * 100 * 100 * 4
     assert lib.brsi_inv_ex(100, 4096, 100, 4, lib.TRI_F32, 256, need - 1) == lib.TRI_ERR_NOMEM
 
+
+def test_tune_cache_file_errors_need_no_gpu(libtri, tmp_path):
+    assert lib.tri_tune_cache_load(str(tmp_path / "missing.json"))[0] == lib.TRI_ERR_ARG
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"version": 1, "entries": [{"key": "x", "threads": 7}]}')
+    assert lib.tri_tune_cache_load(str(bad))[0] == lib.TRI_ERR_ARG
+    good = tmp_path / "good.json"
+    good.write_text('{"version": 1, "entries": [{"key": "cpu-test:1:c2:0,", "threads": 32}]}')
+    assert lib.tri_tune_cache_load(str(good)) == (lib.TRI_OK, 1)
+    out = tmp_path / "out.json"
+    assert lib.tri_tune_cache_save(str(out)) == lib.TRI_OK
+    import json
+    assert any(e["key"] == "cpu-test:1:c2:0," for e in json.load(open(out))["entries"])
+

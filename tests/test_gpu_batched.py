@@ -133,6 +133,8 @@ def test_batched_plan_graph_replay_config_batch(lib):
                                            lib.TRI_F32)
     assert st == lib.TRI_OK
     assert lib.tri_batched_plan_threads(plan) in (256, 512)
+    assert [lib.tri_batched_plan_shape(plan, c)[0] for c in range(3)] == [
+        int(np.sum(sizes > 128)), int(np.sum((sizes > 32) & (sizes <= 128))), int(np.sum(sizes <= 32))]
     s = int(torch.cuda.current_stream().cuda_stream)
     for rep in range(2):
         b.reset()
@@ -147,6 +149,35 @@ def test_batched_plan_graph_replay_config_batch(lib):
     order = np.argsort(sizes)
     sample = list(order[:8]) + list(order[-8:]) + list(range(0, 4096, 257))
     check_blocks([xs[i] for i in sample], [blocks[i] for i in sample], True, False, "f32")
+
+
+def test_batched_size_classes_and_tune_cache(lib, tmp_path):
+    """Blocks of every size class in one plan (129..256 rows, 33..128, up to 32): each class
+    runs with the CTA shape the autotuner picked; the results match the oracle; the tuner's
+    choices round-trip through the JSON tune cache."""
+    import json
+    sizes = [256, 200, 129, 128, 77, 33, 32, 20, 1] * 3
+    rng = np.random.default_rng(11)
+    blocks = [inputs.tri_lower(n, law="uniform", rng=rng).astype(np.float32).astype(np.float64) for n in sizes]
+    b = Batch(blocks, True, "f32")
+    st, plan = lib.tri_batched_plan_create(len(blocks), sizes, b.ptrs, lib.TRI_LOWER, lib.TRI_NONUNIT,
+                                           lib.TRI_F32)
+    assert st == lib.TRI_OK
+    shapes = [lib.tri_batched_plan_shape(plan, c) for c in range(3)]
+    assert [sh[0] for sh in shapes] == [9, 9, 9]
+    assert shapes[0][1] in (256, 512) and shapes[1][1] in (128, 256) and shapes[2][1] in (32, 64)
+    assert all(sh[2] >= 1 for sh in shapes)
+    assert lib.tri_batched_exec(plan, int(torch.cuda.current_stream().cuda_stream)) == lib.TRI_OK
+    torch.cuda.synchronize()
+    check_blocks(b.result(False), blocks, True, False, "f32")
+    assert lib.tri_batched_plan_destroy(plan) == lib.TRI_OK
+    path = str(tmp_path / "tune.json")
+    assert lib.tri_tune_cache_save(path) == lib.TRI_OK
+    doc = json.load(open(path))
+    assert doc["version"] == 1 and len(doc["entries"]) >= 3
+    assert all(e["threads"] in (32, 64, 128, 256, 512) for e in doc["entries"])
+    st, n = lib.tri_tune_cache_load(path)
+    assert st == lib.TRI_OK and n == len(doc["entries"])
 
 
 def test_batched_singular_block_reported(lib):
