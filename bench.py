@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--cpu-sample-stride", type=int, default=1)
     p.add_argument("--profile-config", default=None,
                    choices=["batched_4096", "general_f32_n16384", "adjoint_256x1024", "single_f64_n512",
-                            "combrit_beta", "factor_f32_n16384", "factor_f32_n2048", "brsi_gamma"],
+                            "combrit_beta", "factor_f32_n16384", "factor_f32_n2048", "brsi_gamma",
+                            "batched_4096_plan"],
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
@@ -301,12 +302,15 @@ def secondary(torch, lib, dev, only=None):
     pr = torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
     wk = torch.empty_like(pr)
     res = {}
-    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32)):
+    for name, code in (("mixed", lib.TRI_F32_MIXED), ("plain", lib.TRI_F32), ("mixed_direct", lib.TRI_F32_MIXED)):
+        if name == "mixed_direct":   # six-term products, no Newton-Schulz step (alternative recipe)
+            lib.check(lib.tri_set_mixed_recipe(lib.TRI_RECIPE_DIRECT), "tri_set_mixed_recipe")
         need = lib.gen_inv_workspace_size(n, code)
         ws = torch.empty(need + 256, dtype=torch.uint8, device=dev)
         wp = (ws.data_ptr() + 255) // 256 * 256
         ms = event_time(torch, lambda: lib.check(lib.gen_inv_ex(n, wk.data_ptr(), n, code, wp, need, sh)),
-                        2 if name == "mixed" else 1, 1, setup=lambda: wk.copy_(pr))
+                        1 if name == "plain" else 2, 1, setup=lambda: wk.copy_(pr))
+        lib.check(lib.tri_set_mixed_recipe(lib.TRI_RECIPE_NEWTON_SCHULZ), "tri_set_mixed_recipe")
         cols = [0, 8191, 16383]
         x = wk[cols, :].double()                       # rows of the buffer = columns of X
         ad = pr.T.double()
@@ -327,7 +331,8 @@ def _secondary_rest(torch, lib, dev, out, only):
     from paper_2307_07611_gb300 import inputs
     sh = int(torch.cuda.current_stream().cuda_stream)
     want = lambda name: only is None or only == name
-    if not want("batched_4096"):
+    plan_only = only == "batched_4096_plan"   # the plan alone, without the loop-of-calls baseline
+    if not want("batched_4096") and not plan_only:
         return _secondary_adjoint(torch, lib, dev, out, only)
 
     # batched: 4096 lower FP32 blocks, sizes U{16..256}, one persistent graph-captured launch;
@@ -351,10 +356,12 @@ def _secondary_rest(torch, lib, dev, out, only):
     res = {"value": fl / (ms * 1e-3) / 1e12, "unit": "TFLOP/s (sum n^3/3 over all 4096 blocks)", "ms": ms,
            "threads": lib.tri_batched_plan_threads(plan), "n_gpus": world,
            "dense_bytes_GBps": 2 * 4 * float(sum(float(k) ** 2 for k in sizes_all)) / (ms * 1e-3) / 1e9}
+    res["classes"] = [dict(zip(("blocks", "threads", "ctas"), lib.tri_batched_plan_shape(plan, c)))
+                      for c in range(4)]
     if world > 1:
         res.update({"scaling": "strong", "parallelism": f"blocks partitioned over {world} ranks, no collective",
                     "blocks_on_rank0": len(mine), "rank0_ms": ms_rank})
-    else:
+    elif not plan_only:
         # baseline: the same blocks by a loop of plain tri_inv_ex calls (caller workspace)
         need = max(lib.tri_inv_workspace_size(int(k), lib.TRI_F32) for k in sizes)
         wsb = torch.empty(need + 256, dtype=torch.uint8, device=dev)

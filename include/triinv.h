@@ -272,13 +272,14 @@ TRI_API int tri_batched_plan_threads(const tri_batched_plan *plan);
 
 /* The plan's CTA shape per size class (diagnostic): the blocks are split into classes,
  * each its own persistent launch over a largest-first queue, replayed in order:
- *   cls 0: 129..256 rows (FP32) -- 8 x 8 tiles of 32, one CTA per SM, 256 or 512 threads;
- *   cls 1: 33..128 rows -- 4 x 4 tiles, several CTAs per SM, 128 or 256 threads;
- *   cls 2: up to 32 rows -- one tile, 32 or 64 threads, many CTAs per SM.
+ *   cls 0: 161..256 rows (FP32) -- 8 x 8 tiles of 32, one CTA per SM, 256 or 512 threads;
+ *   cls 1: 129..160 rows (FP32) -- 5 x 5 tiles, two CTAs per SM, 256 or 512 threads;
+ *   cls 2: 33..128 rows -- 4 x 4 tiles, several CTAs per SM, 128 or 256 threads;
+ *   cls 3: up to 32 rows -- one tile, 32 or 64 threads, many CTAs per SM.
  * The autotuner times each candidate thread count (with the CTAs that fit beside it) on a
  * scratch copy of the class's sizes when the plan is created and keeps the fastest.
  * blocks / threads / ctas (each may be NULL): the class's block count, threads per CTA
- * and persistent CTAs.  Errors: TRI_ERR_ARG (null plan, cls outside 0..2). */
+ * and persistent CTAs.  Errors: TRI_ERR_ARG (null plan, cls outside 0..3). */
 TRI_API tri_status tri_batched_plan_shape(const tri_batched_plan *plan, int cls, int *blocks, int *threads,
                                           int *ctas);
 
@@ -476,14 +477,15 @@ TRI_API tri_status tri_get_info(void *stream, int64_t *first_bad_index);
 TRI_API tri_status tri_set_growth_limit(double tau);
 TRI_API double tri_growth_limit(void);
 
-/* Recipe of TRI_F32_MIXED on the triangular paths (tri_inv[_ex], strided batches),
- * process-wide:
+/* Recipe of TRI_F32_MIXED on the triangular paths (tri_inv[_ex], strided batches) and in
+ * gen_inv, process-wide:
  *   TRI_RECIPE_NEWTON_SCHULZ (default)  three-term split-BF16 level products, then one
  *       Newton-Schulz step X <- X + X (I - T X) with a six-term residual and a one-term
  *       update: the result is better than the plain FP32 recursion's.
  *   TRI_RECIPE_DIRECT  the level products take all six split-BF16 terms with FP32
  *       promotion every 64 k (FP32-class products) and there is no Newton-Schulz step:
  *       about the plain FP32 recursion's accuracy, at about 60% of the tensor-core work.
+ *       gen_inv follows the same choice (six-term products, no step against A).
  *       Not part of the paper's method or of the spec recipe; an alternative.
  * Errors: TRI_ERR_ARG (unknown recipe). */
 #define TRI_RECIPE_NEWTON_SCHULZ 0

@@ -417,18 +417,19 @@ KernFn pick3(bool trans, bool unit) {
 }
 
 // Size classes of a batch, each its own persistent launch with its own CTA shape:
-//   class 0  129..256 rows (FP32): 8 x 8 tiles, 220 KB of shared memory, one CTA per SM;
-//   class 1  33..128 rows: 4 x 4 tiles (59 KB FP32, 118 KB FP64), several CTAs per SM;
-//   class 2  up to 32 rows: one tile, one warp per CTA, many CTAs per SM.
+//   class 0  161..256 rows (FP32): 8 x 8 tiles, 220 KB of shared memory, one CTA per SM;
+//   class 1  129..160 rows (FP32): 5 x 5 tiles (80 KB), two CTAs per SM;
+//   class 2  33..128 rows: 4 x 4 tiles (59 KB FP32, 118 KB FP64), several CTAs per SM;
+//   class 3  up to 32 rows: one tile, one warp per CTA, many CTAs per SM.
 // Candidate thread counts per class (the autotuner times them); 0 ends a list.
-constexpr int kClasses = 3;
-constexpr int kCandidates[kClasses][3] = {{512, 256, 0}, {128, 256, 0}, {32, 64, 0}};
+constexpr int kClasses = 4;
+constexpr int kCandidates[kClasses][3] = {{512, 256, 0}, {256, 512, 0}, {128, 256, 0}, {32, 64, 0}};
 
-int size_class(int64_t n) { return n > 128 ? 0 : (n > 32 ? 1 : 2); }
+int size_class(int64_t n) { return n > 160 ? 0 : (n > 128 ? 1 : (n > 32 ? 2 : 3)); }
 
 // Kernel for a precision, orientation, diagonal kind, size class and thread count.
 KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int cls, int threads, size_t *smem) {
-    if (cls == 2) {
+    if (cls == 3) {
         if (dt == TRI_F64) {
             *smem = smem_bytes<double, 1>();
             return threads == 64 ? pick3<double, 1, 64>(trans, unit) : pick3<double, 1, 32>(trans, unit);
@@ -436,7 +437,11 @@ KernFn pick_kernel(tri_dtype dt, bool trans, bool unit, int cls, int threads, si
         *smem = threads == 64 ? smem_bytes<float, 1, 64>() : smem_bytes<float, 1, 32>();
         return threads == 64 ? pick3<float, 1, 64>(trans, unit) : pick3<float, 1, 32>(trans, unit);
     }
-    if (cls == 1) {
+    if (cls == 1) {   // FP32 only (FP64 blocks stop at 128 rows)
+        *smem = threads == 512 ? smem_bytes<float, 5, 512>() : smem_bytes<float, 5, 256>();
+        return threads == 512 ? pick3<float, 5, 512>(trans, unit) : pick3<float, 5, 256>(trans, unit);
+    }
+    if (cls == 2) {
         if (dt == TRI_F64) {
             *smem = smem_bytes<double, 4>();
             return threads == 256 ? pick3<double, 4, 256>(trans, unit) : pick3<double, 4, 128>(trans, unit);
@@ -486,10 +491,10 @@ struct tri_batched_plan {
     triinv::BDesc *d_desc = nullptr;   // sorted, largest first: classes 0, 1, 2 in order
     int *d_counter = nullptr;          // one queue counter per size class
     float *d_tau = nullptr;            // growth limit of the FP64 fallback (device, FP32 plans)
-    int first[3] = {0, 0, 0};          // first descriptor of each size class
-    int nclass[3] = {0, 0, 0};         // blocks of each size class
-    int threads[3] = {0, 0, 0};        // tuned threads per CTA of each class
-    int ctas[3] = {0, 0, 0};           // persistent CTAs of each class
+    int first[4] = {0, 0, 0, 0};       // first descriptor of each size class
+    int nclass[4] = {0, 0, 0, 0};      // blocks of each size class
+    int threads[4] = {0, 0, 0, 0};     // tuned threads per CTA of each class
+    int ctas[4] = {0, 0, 0, 0};        // persistent CTAs of each class
     double flops = 0.0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -589,7 +594,7 @@ int autotune_class(tri_batched_plan *p, int cls, const std::vector<int64_t> &siz
     long long *d_info = nullptr;
     int *d_cnt = nullptr;
     if (cudaMalloc(&scratch, total * es) != cudaSuccess || cudaMalloc(&d_scr, sizeof(BDesc) * sizes.size()) != cudaSuccess ||
-        cudaMalloc(&d_info, sizeof(long long)) != cudaSuccess || cudaMalloc(&d_cnt, 3 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&d_info, sizeof(long long)) != cudaSuccess || cudaMalloc(&d_cnt, kClasses * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(scratch);
         cudaFree(d_scr);

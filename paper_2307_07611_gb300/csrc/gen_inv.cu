@@ -277,10 +277,12 @@ struct GenCtx {
 
 // Mixed products: three terms (about 2^-16 relative) in gen_inv, whose Newton-Schulz step
 // then restores FP32 accuracy against A; six promoted terms (about 2^-24) in SKUL, whose
-// factors are the result and get no refinement.
+// factors are the result and get no refinement, and in gen_inv under the direct recipe
+// (tri_set_mixed_recipe), which then skips the Newton-Schulz step.
 cudaError_t product(const GenCtx &g, const GemmArgs &a, const char *name) {
     if (g.dt == TRI_F32_MIXED && a.m >= kTcMin && a.n >= kTcMin && a.k >= kTcMin)
-        return gemm_tc(*g.c, a, g.keep ? 6 : 3, g.ws + g.lay.ks + g.lay.temps, name);
+        return gemm_tc(*g.c, a, (g.keep || g.c->recipe == TRI_RECIPE_DIRECT) ? 6 : 3,
+                       g.ws + g.lay.ks + g.lay.temps, name);
     return gemm_simt(*g.c, g.dt == TRI_F64 ? TRI_F64 : TRI_F32, a, name);
 }
 
@@ -403,7 +405,7 @@ tri_status run_gen_inv(const Ctx &c, tri_dtype dt, int64_t n, void *a, int64_t l
     g.info_base = info_base;
     uint8_t *ks = (uint8_t *)ws;
     const int64_t ldk = n;
-    const bool ns = g.lay.a0 > 0;
+    const bool ns = g.lay.a0 > 0 && c.recipe != TRI_RECIPE_DIRECT;
     float *a0 = ns ? (float *)(g.ws + g.lay.ks + g.lay.temps + g.lay.planes) : nullptr;
     cudaError_t e = cudaSuccess;
     if (ns) e = cudaMemcpy2DAsync(a0, n * 4, a, lda * 4, n * 4, n, cudaMemcpyDeviceToDevice, c.stream);

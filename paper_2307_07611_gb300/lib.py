@@ -231,7 +231,7 @@ def tri_batched_plan_threads(plan) -> int:
 
 
 def tri_batched_plan_shape(plan, cls):
-    """(blocks, threads, ctas) of size class cls (0: 129..256 rows, 1: 33..128, 2: <= 32)."""
+    """(blocks, threads, ctas) of size class cls (0: 161..256 rows, 1: 129..160, 2: 33..128, 3: <= 32)."""
     b, t, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     check(load().tri_batched_plan_shape(plan, int(cls), ctypes.byref(b), ctypes.byref(t), ctypes.byref(c)),
           "tri_batched_plan_shape")

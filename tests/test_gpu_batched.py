@@ -133,8 +133,9 @@ def test_batched_plan_graph_replay_config_batch(lib):
                                            lib.TRI_F32)
     assert st == lib.TRI_OK
     assert lib.tri_batched_plan_threads(plan) in (256, 512)
-    assert [lib.tri_batched_plan_shape(plan, c)[0] for c in range(3)] == [
-        int(np.sum(sizes > 128)), int(np.sum((sizes > 32) & (sizes <= 128))), int(np.sum(sizes <= 32))]
+    assert [lib.tri_batched_plan_shape(plan, c)[0] for c in range(4)] == [
+        int(np.sum(sizes > 160)), int(np.sum((sizes > 128) & (sizes <= 160))),
+        int(np.sum((sizes > 32) & (sizes <= 128))), int(np.sum(sizes <= 32))]
     s = int(torch.cuda.current_stream().cuda_stream)
     for rep in range(2):
         b.reset()
@@ -152,7 +153,7 @@ def test_batched_plan_graph_replay_config_batch(lib):
 
 
 def test_batched_size_classes_and_tune_cache(lib, tmp_path):
-    """Blocks of every size class in one plan (129..256 rows, 33..128, up to 32): each class
+    """Blocks of every size class in one plan (161..256 rows, 129..160, 33..128, up to 32): each class
     runs with the CTA shape the autotuner picked; the results match the oracle; the tuner's
     choices round-trip through the JSON tune cache."""
     import json
@@ -163,9 +164,10 @@ def test_batched_size_classes_and_tune_cache(lib, tmp_path):
     st, plan = lib.tri_batched_plan_create(len(blocks), sizes, b.ptrs, lib.TRI_LOWER, lib.TRI_NONUNIT,
                                            lib.TRI_F32)
     assert st == lib.TRI_OK
-    shapes = [lib.tri_batched_plan_shape(plan, c) for c in range(3)]
-    assert [sh[0] for sh in shapes] == [9, 9, 9]
-    assert shapes[0][1] in (256, 512) and shapes[1][1] in (128, 256) and shapes[2][1] in (32, 64)
+    shapes = [lib.tri_batched_plan_shape(plan, c) for c in range(4)]
+    assert [sh[0] for sh in shapes] == [6, 3, 9, 9]
+    assert shapes[0][1] in (256, 512) and shapes[1][1] in (256, 512) and shapes[2][1] in (128, 256)
+    assert shapes[3][1] in (32, 64)
     assert all(sh[2] >= 1 for sh in shapes)
     assert lib.tri_batched_exec(plan, int(torch.cuda.current_stream().cuda_stream)) == lib.TRI_OK
     torch.cuda.synchronize()
@@ -174,7 +176,7 @@ def test_batched_size_classes_and_tune_cache(lib, tmp_path):
     path = str(tmp_path / "tune.json")
     assert lib.tri_tune_cache_save(path) == lib.TRI_OK
     doc = json.load(open(path))
-    assert doc["version"] == 1 and len(doc["entries"]) >= 3
+    assert doc["version"] == 1 and len(doc["entries"]) >= 4
     assert all(e["threads"] in (32, 64, 128, 256, 512) for e in doc["entries"])
     st, n = lib.tri_tune_cache_load(path)
     assert st == lib.TRI_OK and n == len(doc["entries"])

@@ -58,3 +58,22 @@ def test_direct_equal_residual(lib, n):
 def test_recipe_setting(lib):
     assert lib.tri_set_mixed_recipe(7) == lib.TRI_ERR_ARG
     assert lib.tri_mixed_recipe() == lib.TRI_RECIPE_DIRECT
+
+
+@pytest.mark.parametrize("n", [600, 2000])
+def test_direct_gen_inv(lib, n):
+    """gen_inv under the direct recipe: six-term products, no Newton-Schulz step; FP32
+    tolerance against the oracle and equal residual against plain FP32."""
+    a = inputs.general(n, seed=n, dtype=np.float32).astype(np.float64)
+
+    def run(code):
+        dev = torch.from_numpy(np.ascontiguousarray(a.T).astype(np.float32)).cuda()
+        assert lib.gen_inv(n, dev.data_ptr(), n, code, int(torch.cuda.current_stream().cuda_stream)) == lib.TRI_OK
+        torch.cuda.synchronize()
+        return dev.cpu().numpy().T.astype(np.float64)
+
+    xd, xp = run(lib.TRI_F32_MIXED), run(lib.TRI_F32)
+    want = oracle.gen_inv(a)
+    assert np.abs(xd - want).max() / np.abs(want).max() <= tol(n)
+    res = lambda x: np.linalg.norm(a @ x - np.eye(n)) / (np.linalg.norm(a) * np.linalg.norm(x))
+    assert res(xd) <= 2.0 * res(xp), (res(xd), res(xp))
