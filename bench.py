@@ -53,6 +53,9 @@ def parse():
                    help="run only this secondary workload once (for profiler captures) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the secondary workloads (FP64 n=512, general n=16384, batched, adjoint)")
+    p.add_argument("--cta-pairs", type=int, default=None,
+                   help="mask of mixed-path products run on CTA pairs (tri_set_cta_pairs: 1 levels, "
+                        "2 residual, 4 update); default: the library's")
     return p.parse_args()
 
 
@@ -101,12 +104,15 @@ def dominant_traffic(kernel: str):
     or None if there is none or the kernel source changed since it was captured."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic_n8192.json")
-    src = os.path.join(ROOT, "paper_2307_07611_gb300", "csrc", f"{kernel}.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        # the kernel's sources, hashed in the recorded order (default: <kernel>.cu)
+        h = hashlib.sha256()
+        for name in rec.get("sources", [f"{kernel}.cu"]):
+            with open(os.path.join(ROOT, "paper_2307_07611_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        digest = h.hexdigest()
         if rec.get("source_sha256") != digest:
             return None
         return float(rec["dram_bytes_per_launch"])
@@ -601,6 +607,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib.load()
+    if args.cta_pairs is not None:
+        lib.check(lib.tri_set_cta_pairs(args.cta_pairs), "tri_set_cta_pairs")
 
     mode = args.mode
     if mode == "auto":
@@ -801,7 +809,9 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "mode": mode, "leaf": 64,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (268 MB per matrix)",
-                       "restore": "untimed device copy of T before each step"},
+                       "restore": "untimed device copy of T before each step",
+                       "cta_pairs": lib.tri_cta_pairs(),
+                       "cta_pair_capacity": lib.tri_cta_pair_capacity() if lib.tri_cta_pairs() else None},
             "residual": resid, "max_rel_err_vs_oracle_cols": err,
             "info_status": st_info,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -493,6 +493,28 @@ TRI_API double tri_growth_limit(void);
 TRI_API tri_status tri_set_mixed_recipe(int recipe);
 TRI_API int tri_mixed_recipe(void);
 
+/* Products of the TRI_F32_MIXED triangular path (single matrices and strided batches,
+ * Newton-Schulz recipe) that run on CTA pairs, process-wide: a bit mask of
+ *   TRI_PAIR_LEVELS  the level products W = B X_A and X21 = -X_C W at split half-sizes
+ *                    whose output tiles are 256 columns wide,
+ *   TRI_PAIR_RES     the residual R = I - T X,
+ *   TRI_PAIR_UPD     the update X += X R.
+ * A pair is a cluster of two CTAs on two SMs that computes each 256 x 256 output tile with
+ * one 256-row tensor-core product per k-step (tcgen05.mma.cta_group::2), each CTA staging
+ * its own 128 rows of the left operand and half of the right one's tile: the same
+ * products, summed in the same order (results are bit-identical to the single-CTA
+ * schedule), with a third less operand traffic into each SM.  A schedule choice, not part
+ * of the paper's method.  tri_cta_pairs returns the current mask.
+ * Errors: TRI_ERR_ARG (bits outside the three). */
+#define TRI_PAIR_LEVELS 1
+#define TRI_PAIR_RES 2
+#define TRI_PAIR_UPD 4
+TRI_API tri_status tri_set_cta_pairs(int mask);
+TRI_API int tri_cta_pairs(void);
+/* CTA pairs of the product kernel that the current device runs at once (the number of
+ * tile lists of a pair launch); 0 if the device cannot be queried. */
+TRI_API int tri_cta_pair_capacity(void);
+
 /* Measured CUDA-core peak of the current device for dtype TRI_F32 (FFMA) or TRI_F64
  * (DFMA), in TFLOP/s (2 flops per fused multiply-add): every thread of a full grid runs 8
  * independent chains of `iters` dependent FMAs, timed with CUDA events after a warm-up.

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace triinv {
 
@@ -48,6 +49,7 @@ std::atomic<float> g_growth_tau{1.0e4f};
 
 // Recipe of the mixed triangular path (process-wide).
 std::atomic<int> g_recipe{TRI_RECIPE_NEWTON_SCHULZ};
+std::atomic<int> g_pairs{0};
 
 tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     int dev = 0;
@@ -71,6 +73,7 @@ tri_status device_ctx(cudaStream_t stream, Ctx *out) {
     out->device = dev;
     out->tau = g_growth_tau.load(std::memory_order_relaxed);
     out->recipe = g_recipe.load(std::memory_order_relaxed);
+    out->pairs = g_pairs.load(std::memory_order_relaxed);
     return TRI_OK;
 }
 
@@ -636,6 +639,20 @@ tri_status tri_set_mixed_recipe(int recipe) {
 }
 
 int tri_mixed_recipe(void) { return g_recipe.load(std::memory_order_relaxed); }
+
+tri_status tri_set_cta_pairs(int mask) {
+    if (mask & ~(TRI_PAIR_LEVELS | TRI_PAIR_RES | TRI_PAIR_UPD)) return TRI_ERR_ARG;
+    g_pairs.store(mask, std::memory_order_relaxed);
+    return TRI_OK;
+}
+
+int tri_cta_pairs(void) { return g_pairs.load(std::memory_order_relaxed); }
+
+int tri_cta_pair_capacity(void) {
+    Ctx c;
+    if (device_ctx_public(nullptr, &c) != TRI_OK) return 0;
+    return tc::pair_lists(c);
+}
 
 tri_status tri_pool_stats(uint64_t *used, uint64_t *used_high, int reset_high) {
     cudaMemPool_t pool;

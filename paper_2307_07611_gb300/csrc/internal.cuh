@@ -19,6 +19,7 @@ struct Ctx {
     float tau;         // growth limit of the FP64 fallback for ill-conditioned diagonal
                        // blocks (tri_set_growth_limit; <= 0 disables)
     int recipe;        // TRI_F32_MIXED recipe of the triangular path (tri_set_mixed_recipe)
+    int pairs;         // products of the mixed path run on CTA pairs (tri_set_cta_pairs)
 };
 
 // Lower-orientation view of a column-major matrix.  For an upper-triangular matrix U

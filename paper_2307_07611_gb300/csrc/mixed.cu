@@ -116,7 +116,11 @@ struct Launch {
     int first, ctas, off_first;   // tiles from `first`, CTA offsets from `off_first`
     double flops;
     int bn = tc::BN;              // output tile width the tiles were cut with
+    bool pair = false;            // 256-row tiles for clusters of two CTAs
 };
+
+// Products run by CTA pairs (tc_gemm_pair.cu, tri_set_cta_pairs).
+constexpr int kPairLevels = TRI_PAIR_LEVELS, kPairRes = TRI_PAIR_RES, kPairUpd = TRI_PAIR_UPD;
 
 // Output tile width of the level products at split half-size h.  A level's products
 // are P = n / 2h pairs of h x h "triangular x full" products; with 128 x 256 tiles the low
@@ -166,16 +170,17 @@ bool use_graph_schedule() {
 }
 
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int64_t, int64_t, int>, Plan> g_plans;
+std::map<std::tuple<int, int64_t, int64_t, int, int>, Plan> g_plans;
 
 // Tile lists of every product for `batch` matrices of order n (each product's tiles of
 // all matrices in one longest-first schedule).  recipe TRI_RECIPE_DIRECT: the level
 // products take six terms (longest-first costs follow) and there is no Newton-Schulz step.
-tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recipe, Plan **out) {
+tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64_t batch, int recipe, Plan **out) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     const bool direct = recipe == TRI_RECIPE_DIRECT;
     const int lterms = direct ? 6 : 3;
-    auto key = std::make_tuple(dev, n, batch, recipe);
+    if (direct) pm = 0;
+    auto key = std::make_tuple(dev, n, batch, recipe, pm);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {
         *out = &it->second;
@@ -184,7 +189,8 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recip
     Plan p;
     std::vector<tc::Tile> v;
     std::vector<int> offs;
-    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms, int bn = tc::BN) {
+    auto add = [&](std::vector<Launch> *vec, Launch *one, size_t from, double flops, int terms, int bn = tc::BN,
+                   bool pair = false) {
         // replicate the single-matrix tiles over the batch
         const size_t one_count = v.size() - from;
         for (int64_t b = 1; b < batch; ++b)
@@ -195,9 +201,9 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recip
             }
         std::vector<tc::Tile> part(v.begin() + from, v.end());
         std::vector<int> o;
-        const int ctas = part.empty() ? 0 : tc::schedule_lpt(part, terms, sm_count, o);
+        const int lists = part.empty() ? 0 : tc::schedule_lpt(part, terms, pair ? pairs : sm_count, o);
         std::copy(part.begin(), part.end(), v.begin() + from);
-        Launch l{(int)from, ctas, (int)offs.size(), flops * (double)batch, bn};
+        Launch l{(int)from, pair ? 2 * lists : lists, (int)offs.size(), flops * (double)batch, bn, pair};
         for (int x : o) offs.push_back(x);
         if (vec) vec->push_back(l);
         else *one = l;
@@ -205,6 +211,9 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recip
     for (int64_t h = kDiag; h < n; h *= 2) {
         const int64_t P = level_pairs(n, h);
         const int bn = level_tile_n(h);   // divides h (h is 256 * 2^s)
+        // full-width three-term level products may run on CTA pairs (256-row tiles)
+        const bool lp = (pm & kPairLevels) && bn == tc::BN;
+        const int64_t bm = lp ? tc::PAIR_BM : tc::BM;
         // W = B X_A  (W is h x P*h, pair q in columns [q*h, q*h + h))
         size_t from = v.size();
         double fl = 0.0;
@@ -212,40 +221,42 @@ tri_status build_plan(int dev, int sm_count, int64_t n, int64_t batch, int recip
             const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
             fl += lterms * (double)hc * h * (h + 1);
             for (int64_t tn = 0; tn < h / bn; ++tn)
-                for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm)
-                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * bn),
+                for (int64_t tm = 0; tm < cdiv(hc, bm); ++tm)
+                    v.push_back(tc::Tile{(int)(c0 + tm * bm), (int)a0, (int)a0, (int)(a0 + tn * bn),
                                          (int)(tn * bn / tc::BK), (int)(h / tc::BK),
-                                         (int)(tm * tc::BM), (int)(q * h + tn * bn)});
+                                         (int)(tm * bm), (int)(q * h + tn * bn)});
         }
-        add(&p.w, nullptr, from, fl, lterms, bn);
+        add(&p.w, nullptr, from, fl, lterms, bn, lp);
         // X21 = -X_C W
         from = v.size();
         fl = 0.0;
         for (int64_t q = 0; q < P; ++q) {
             const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
             fl += lterms * (double)h * hc * (hc + 1);
-            for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
-                const int64_t kend = std::min((tm + 1) * tc::BM, hc);
+            for (int64_t tm = 0; tm < cdiv(hc, bm); ++tm) {
+                const int64_t kend = std::min((tm + 1) * bm, hc);
                 for (int64_t tn = 0; tn < h / bn; ++tn)
-                    v.push_back(tc::Tile{(int)(c0 + tm * tc::BM), (int)c0, 0, (int)(q * h + tn * bn), 0,
-                                         (int)cdiv(kend, tc::BK), (int)(c0 + tm * tc::BM),
+                    v.push_back(tc::Tile{(int)(c0 + tm * bm), (int)c0, 0, (int)(q * h + tn * bn), 0,
+                                         (int)cdiv(kend, tc::BK), (int)(c0 + tm * bm),
                                          (int)(a0 + tn * bn)});
             }
         }
-        add(&p.x21, nullptr, from, fl, lterms, bn);
+        add(&p.x21, nullptr, from, fl, lterms, bn, lp);
     }
     // Newton-Schulz: lower x lower products over the whole matrix.
     const double lower_prod = (double)n * (n + 1) * (n + 2) / 3.0;   // 2 * sum_{i>=j} (i-j+1)
     for (int pass = 0; pass < (direct ? 0 : 2); ++pass) {
         const size_t from = v.size();
-        for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
-            const int64_t kend = std::min((tm + 1) * tc::BM, n);
+        const bool pp = (pm & (pass == 0 ? kPairRes : kPairUpd)) != 0;
+        const int64_t bm = pp ? tc::PAIR_BM : tc::BM;
+        for (int64_t tm = 0; tm < cdiv(n, bm); ++tm) {
+            const int64_t kend = std::min((tm + 1) * bm, n);
             for (int64_t tn = 0; tn * tc::BN < kend; ++tn)
-                v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
-                                     (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
+                v.push_back(tc::Tile{(int)(tm * bm), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
+                                     (int)cdiv(kend, tc::BK), (int)(tm * bm), (int)(tn * tc::BN)});
         }
         add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 1.0) * lower_prod,
-            pass == 0 ? 6 : 1);
+            pass == 0 ? 6 : 1, tc::BN, pp);
     }
     if (!v.empty()) {
         const size_t tb = v.size() * sizeof(tc::Tile), ob = offs.size() * sizeof(int);
@@ -311,7 +322,8 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     const tc::GraphPlan *gplan = nullptr;
     Plan *plan = nullptr;
     tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan)
-                          : build_plan(c.device, c.sm_count, n, batch, c.recipe, &plan);
+                          : build_plan(c.device, c.sm_count, c.pairs ? tc::pair_lists(c) : 0, c.pairs, n, batch,
+                                       c.recipe, &plan);
     if (st != TRI_OK) return st;
 
     // 1. T planes of the off-diagonal part (side stream), concurrently with
@@ -369,14 +381,14 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         ew.os = ps;
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, mw, trans, unit, tp, 3, xp, 3, lt, plan->d_tiles + lw.first, plan->d_off + lw.off_first,
-                          lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn) != cudaSuccess)
+                          lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn, lw.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         ex.xs = stride;
         ex.os = ps;
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, mx, trans, unit, xp, 3, wp, nw, lt, plan->d_tiles + lx.first, plan->d_off + lx.off_first,
-                          lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn) != cudaSuccess)
+                          lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn, lx.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
     if (direct) return TRI_OK;
@@ -388,14 +400,16 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         er.skip_n = (int)((n + kDiag - 1) / kDiag);
     }
     if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
-                      plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res") != cudaSuccess)
+                      plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res", tc::BN,
+                      plan->res.pair) != cudaSuccess)
         return TRI_ERR_CUDA;
     const tc::Plane rp[1] = {pl(R[0], n, n, L.ldp)};
     const tc::Terms one{1, {0}, {0}};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
     eu.xs = stride;
     if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + plan->upd.first,
-                      plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd") != cudaSuccess)
+                      plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd", tc::BN,
+                      plan->upd.pair) != cudaSuccess)
         return TRI_ERR_CUDA;
     return TRI_OK;
 }

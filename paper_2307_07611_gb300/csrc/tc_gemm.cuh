@@ -85,10 +85,19 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
 // by `terms`.
 // bn: columns of the output tiles the list was built with: BN, or 128 / 64 for the level
 // products (MODE_W, MODE_X21, MODE_W6, MODE_X216).
+// pair: the list holds 256-row tiles (BN wide; MODE_W, MODE_X21, MODE_RES, MODE_UPD), each
+// computed by a cluster of two CTAs; `ctas` is twice the number of lists.
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
                       int na, const Plane *bplanes, int nb, const Terms &terms,
                       const Tile *d_tiles, const int *d_off, int ctas, const Epi &epi,
-                      double flops, const char *trace_name, int bn = BN);
+                      double flops, const char *trace_name, int bn = BN, bool pair = false);
+
+// Rows of the output tiles of a CTA-pair launch.
+constexpr int PAIR_BM = 2 * BM;
+
+// Number of CTA pairs of the product kernel that can run at once on this device (at least
+// 1; cached per device).
+int pair_lists(const Ctx &c);
 
 }  // namespace tc
 }  // namespace triinv

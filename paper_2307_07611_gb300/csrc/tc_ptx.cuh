@@ -24,10 +24,10 @@ constexpr unsigned long long kWaitLimitNs = 4000000000ull;   // 4 s per wait
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9,
 // 10-12 = 1), A MN-major (bit 15), B K-major (bit 16 = 0), N >> 3 at bits 17-22,
-// M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_for(int n) {
+// M >> 4 at bits 24-28.  m = 256 is the M of a CTA-pair product (128 rows per CTA).
+__host__ __device__ constexpr uint32_t idesc_for(int n, int m = BM) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
+           ((uint32_t)(m >> 4) << 24);
 }
 constexpr uint32_t kIdesc = idesc_for(BN);
 
@@ -55,6 +55,36 @@ static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t pari
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Arrive on an mbarrier given by its shared::cluster address (this CTA's or the peer's).
+static __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// shared::cluster address of the variable at shared::cta address `addr` in CTA `rank` of
+// this cluster.
+static __device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+static __device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+static __device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster: release what came before, acquire the others'.
+static __device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 static __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -102,6 +132,26 @@ static __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorM
         : "memory");
 }
 
+// CTA-pair forms: the copy lands in this CTA's shared memory and completes its bytes on
+// the barrier `cluster_bar` (a shared::cluster address, here the even CTA's).
+static __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                                        uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+static __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                                        uint32_t cluster_bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
 static __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                                    uint32_t bar) {
     asm volatile(
@@ -127,6 +177,21 @@ static __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
+// CTA-pair forms (a kernel uses either these or the cta_group::1 forms throughout).
+// The commit arrives, once the products issued so far by this thread complete, on the
+// barrier at the same shared-memory offset in every CTA of cta_mask.
+static __device__ __forceinline__ void tc_commit_pair(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+static __device__ __forceinline__ void tc_commit_pair_mc(uint32_t bar, uint16_t cta_mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(cta_mask)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4
 // (32-45), version 1 (46-47), base offset 0, swizzle mode (61-63).
 // Swizzle modes (bits 61-63): 2 = 128-byte, 4 = 64-byte.
@@ -148,6 +213,19 @@ static __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// CTA-pair product (issued by one thread of the even CTA): D rows 0-127 in this CTA's
+// tensor memory, 128-255 in the peer's; A rows from each CTA's own shared memory, B columns
+// 0 .. N/2-1 from this CTA's and N/2 .. N-1 from the peer's, at the same descriptors.
+static __device__ __forceinline__ void tc_mma_pair(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                                   uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
         : "memory");
 }

@@ -86,6 +86,9 @@ def _declare(lib):
                                    ctypes.POINTER(ctypes.c_double)], i32),
         "tri_set_mixed_recipe": ([i32], i32),
         "tri_mixed_recipe": ([], i32),
+        "tri_set_cta_pairs": ([i32], i32),
+        "tri_cta_pairs": ([], i32),
+        "tri_cta_pair_capacity": ([], i32),
         "tri_set_growth_limit": ([ctypes.c_double], i32),
         "tri_growth_limit": ([], ctypes.c_double),
         "tri_alu_peak": ([i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -362,6 +365,24 @@ def tri_set_mixed_recipe(recipe: int) -> int:
 
 def tri_mixed_recipe() -> int:
     return int(load().tri_mixed_recipe())
+
+
+TRI_PAIR_LEVELS = 1
+TRI_PAIR_RES = 2
+TRI_PAIR_UPD = 4
+TRI_PAIR_ALL = TRI_PAIR_LEVELS | TRI_PAIR_RES | TRI_PAIR_UPD
+
+
+def tri_set_cta_pairs(mask: int) -> int:
+    return load().tri_set_cta_pairs(int(mask))
+
+
+def tri_cta_pairs() -> int:
+    return int(load().tri_cta_pairs())
+
+
+def tri_cta_pair_capacity() -> int:
+    return int(load().tri_cta_pair_capacity())
 
 
 def tri_set_growth_limit(tau: float) -> int:

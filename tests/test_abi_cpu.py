@@ -233,3 +233,14 @@ def test_tune_cache_file_errors_need_no_gpu(libtri, tmp_path):
     import json
     assert any(e["key"] == "cpu-test:1:c2:0," for e in json.load(open(out))["entries"])
 
+
+
+def test_process_settings_need_no_gpu(libtri):
+    """The process-wide settings (growth limit, mixed recipe, CTA-pair products) validate
+    their argument and round-trip without a device."""
+    assert lib.tri_set_cta_pairs(8) == lib.TRI_ERR_ARG
+    assert lib.tri_set_cta_pairs(lib.TRI_PAIR_LEVELS | lib.TRI_PAIR_UPD) == lib.TRI_OK
+    assert lib.tri_cta_pairs() == lib.TRI_PAIR_LEVELS | lib.TRI_PAIR_UPD
+    assert lib.tri_set_cta_pairs(0) == lib.TRI_OK
+    assert lib.tri_set_mixed_recipe(5) == lib.TRI_ERR_ARG
+    assert lib.tri_mixed_recipe() == lib.TRI_RECIPE_NEWTON_SCHULZ
