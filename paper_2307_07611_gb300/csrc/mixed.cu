@@ -373,6 +373,12 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     const int mw = direct ? tc::MODE_W6 : tc::MODE_W, mx = direct ? tc::MODE_X216 : tc::MODE_X21;
     const tc::Terms &lt = direct ? six : three;
     const int nw = direct ? 3 : 2;
+    // trace names per split half-size h = 256 * 2^lvl
+    static const char *const kWName[] = {"tc_gemm:w:256", "tc_gemm:w:512", "tc_gemm:w:1024", "tc_gemm:w:2048",
+                                         "tc_gemm:w:4096", "tc_gemm:w:8192", "tc_gemm:w:16384", "tc_gemm:w"};
+    static const char *const kXName[] = {"tc_gemm:x21:256", "tc_gemm:x21:512", "tc_gemm:x21:1024",
+                                         "tc_gemm:x21:2048", "tc_gemm:x21:4096", "tc_gemm:x21:8192",
+                                         "tc_gemm:x21:16384", "tc_gemm:x21"};
     int lvl = 0;
     for (int64_t h = kDiag; h < n; h *= 2, ++lvl) {
         const int64_t P = level_pairs(n, h);
@@ -381,14 +387,14 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         ew.os = ps;
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, mw, trans, unit, tp, 3, xp, 3, lt, plan->d_tiles + lw.first, plan->d_off + lw.off_first,
-                          lw.ctas, ew, lw.flops, "tc_gemm:w", lw.bn, lw.pair) != cudaSuccess)
+                          lw.ctas, ew, lw.flops, kWName[std::min(lvl, 7)], lw.bn, lw.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         ex.xs = stride;
         ex.os = ps;
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, mx, trans, unit, xp, 3, wp, nw, lt, plan->d_tiles + lx.first, plan->d_off + lx.off_first,
-                          lx.ctas, ex, lx.flops, "tc_gemm:x21", lx.bn, lx.pair) != cudaSuccess)
+                          lx.ctas, ex, lx.flops, kXName[std::min(lvl, 7)], lx.bn, lx.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
     if (direct) return TRI_OK;
