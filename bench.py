@@ -424,7 +424,7 @@ def _secondary_adjoint(torch, lib, dev, out, only):
 
 
 def _secondary_combrit(torch, lib, dev, out, only):
-    """COMBRIT with beta = 2, 4, 8 blocks per level (the paper's comparison of block
+    """COMBRIT with beta = 2, 4, 8, 16 blocks per level (the paper's comparison of block
     counts, Table tab:combrit): FP64 n = 1024 (the paper's largest size, uniform law) and
     FP32 n = 8192 (normal law), TFLOP/s by the n^3/3 convention."""
     import numpy as np
@@ -439,7 +439,7 @@ def _secondary_combrit(torch, lib, dev, out, only):
         pr = torch.from_numpy(np.ascontiguousarray(t.T)).to(tdt).to(dev)
         wk = torch.empty_like(pr)
         row = {}
-        for beta in (2, 4, 8):
+        for beta in (2, 4, 8, 16):
             ms = event_time(torch, lambda: lib.check(lib.tri_inv_combrit(0, 0, n, wk.data_ptr(), n, dt, beta, sh)),
                             5, 2, setup=lambda: wk.copy_(pr))
             row[f"beta{beta}"] = {"ms": ms, "value": n ** 3 / 3 / (ms * 1e-3) / 1e12}

@@ -317,13 +317,13 @@ TRI_API tri_status tri_batched_partition(int64_t count, const int64_t *sizes, in
 
 /* ---------------------------------------------------------------------------------
  * tri_inv_combrit -- the same in-place inverse by Algorithm COMBRIT (Section 4.1) with
- * `beta` diagonal blocks per recursion level (beta = 2, 4 or 8; beta = 2 is the split of
+ * `beta` diagonal blocks per recursion level (beta = 2, 4, 8 or 16; beta = 2 is the split of
  * tri_inv).  Per level, with the beta diagonal inverses X_ii in place: B_ij = X_ii T_ij
  * (the unit block form T*), the unit block inverse W = B^-1 by the block version of the
  * main Theorem (Section 3), then X_ij = W_ij X_jj.  Leaves (64, FP64: 16) use the CRIT
  * recurrence.  TRI_F32 / TRI_F64 only (CUDA-core products); scratch for the B and W
  * blocks of one level (at most n*n elements) comes from the stream-ordered allocator.
- * Errors: as tri_inv; TRI_ERR_ARG for beta not in {2, 4, 8}; TRI_ERR_UNSUPPORTED for
+ * Errors: as tri_inv; TRI_ERR_ARG for beta not in {2, 4, 8, 16}; TRI_ERR_UNSUPPORTED for
  * TRI_F32_MIXED.
  * --------------------------------------------------------------------------------- */
 TRI_API tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda,

@@ -381,7 +381,7 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
 
 tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, tri_dtype dtype,
                            int beta, void *stream) {
-    if (!valid_enums(uplo, diag, dtype) || n < 0 || !(beta == 2 || beta == 4 || beta == 8)) return TRI_ERR_ARG;
+    if (!valid_enums(uplo, diag, dtype) || n < 0 || !(beta == 2 || beta == 4 || beta == 8 || beta == 16)) return TRI_ERR_ARG;
     if (dtype == TRI_F32_MIXED) return TRI_ERR_UNSUPPORTED;
     if (n == 0) return TRI_OK;
     if (!a || lda < std::max<int64_t>(1, n)) return TRI_ERR_ARG;

@@ -1,4 +1,4 @@
-// combrit.cu -- Algorithm COMBRIT (Section 4.1) with beta blocks per level (beta = 2, 4, 8),
+// combrit.cu -- Algorithm COMBRIT (Section 4.1) with beta blocks per level (beta = 2, 4, 8, 16),
 // on CUDA cores (FP32 FFMA / FP64 DFMA).
 //
 // A lower triangular T of order n is walked bottom-up: the leaves (64, or 16 in FP64) are

@@ -152,8 +152,8 @@ def test_mixed_schedule_small_grids_and_errors(libtri):
 
 def test_combrit_argument_errors_need_no_gpu(libtri):
     A = lib.TRI_ERR_ARG
-    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 3) == A          # beta not 2/4/8
-    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 16) == A
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 3) == A          # beta not 2/4/8/16
+    assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32, 32) == A
     assert lib.tri_inv_combrit(0, 0, -1, 4096, 16, lib.TRI_F32, 4) == A
     assert lib.tri_inv_combrit(0, 0, 16, 4096, 16, lib.TRI_F32_MIXED, 4) == lib.TRI_ERR_UNSUPPORTED
     assert lib.tri_inv_combrit(0, 0, 0, 0, 1, lib.TRI_F64, 8) == lib.TRI_OK       # n == 0: no-op

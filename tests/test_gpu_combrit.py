@@ -1,4 +1,4 @@
-"""GPU parity of tri_inv_combrit (Algorithm COMBRIT, Section 4.1, with beta = 2, 4, 8
+"""GPU parity of tri_inv_combrit (Algorithm COMBRIT, Section 4.1, with beta = 2, 4, 8, 16
 diagonal blocks per level) against the FP64 oracle.  Same tolerances as the plain path
 (40 sqrt(n) u max|X| against the oracle, normwise residual 5e-6 / 1e-13); integer families
 whose inverses are small integers are exact; only the referenced triangle is written
@@ -26,7 +26,7 @@ def lib():
     return _lib
 
 
-@pytest.mark.parametrize("beta", [2, 4, 8])
+@pytest.mark.parametrize("beta", [2, 4, 8, 16])
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("n", [1, 17, 64, 200, 1000, 1537, 2048])
 def test_combrit_lower_parity(lib, beta, dt, n):
@@ -40,7 +40,7 @@ def test_combrit_lower_parity(lib, beta, dt, n):
     assert normwise_residual(t, x) <= RESID[dt]
 
 
-@pytest.mark.parametrize("beta", [4, 8])
+@pytest.mark.parametrize("beta", [4, 8, 16])
 @pytest.mark.parametrize("lower,unit", [(False, False), (True, True), (False, True)])
 def test_combrit_uplo_diag(lib, beta, lower, unit):
     n = 777
@@ -53,7 +53,7 @@ def test_combrit_uplo_diag(lib, beta, lower, unit):
     assert rel_max_err(x, want) <= 40 * np.sqrt(n) * U["f64"]
 
 
-@pytest.mark.parametrize("beta", [2, 4, 8])
+@pytest.mark.parametrize("beta", [2, 4, 8, 16])
 def test_combrit_integer_families_bit_exact(lib, beta):
     for t in (inputs.ones_unit_lower(600), inputs.bidiagonal_unit_lower(1100, seed=1)[0],
               inputs.level_nilpotent_unit_lower(1024, 256, seed=2)[0]):
