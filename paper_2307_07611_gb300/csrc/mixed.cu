@@ -19,10 +19,11 @@
 // Direct recipe (tri_set_mixed_recipe(TRI_RECIPE_DIRECT)): the level products of step 4
 // take all six terms with FP32 promotion every 64 k (FP32-class products, W with its lo
 // plane) and step 5 is left out.
-// Steps 4 and 5 run either as one persistent tensor-core launch per product (default)
-// or as a single launch that follows the data dependencies tile by tile (tc_graph.cu,
-// TRI_MIXED_SCHEDULE=graph).  Tile lists and schedules depend on n only and are built
-// once per (device, n).
+// Steps 4 and 5 run either as one persistent tensor-core launch per product (default),
+// with the low levels h = 256 .. 1024 in one dependency-ordered launch
+// (TRI_MIXED_SCHEDULE=merged), or as a single launch that follows the data dependencies
+// tile by tile (tc_graph.cu, TRI_MIXED_SCHEDULE=graph).  Tile lists and schedules depend
+// on n only and are built once per (device, n).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -33,6 +34,7 @@
 #include <vector>
 
 #include "tc_graph.cuh"
+#include "tc_ptx.cuh"
 
 namespace triinv {
 
@@ -84,13 +86,37 @@ struct Layout {
     int64_t ldp;
     size_t plane;                 // bytes of one plane of one matrix (256-aligned)
     int64_t batch;                // matrices whose planes the workspace holds
-    size_t off_t, off_x, off_r, off_w, off_f, off_g, total;
+    size_t off_t, off_x, off_r, off_w, off_f, off_g, off_c, off_m, total;
+    size_t mplane;                // bytes of one merged-level W plane of one matrix
 };
+
+// Under the "merged" schedule the low split levels h = 256 .. kMergedMax (h < n) run as
+// one launch whose tiles wait on dependency counters: two per pair and level (its W tiles
+// done, its X21 tiles done).
+constexpr int64_t kMergedMax = 1024;
+bool use_merged_levels();
+int64_t merged_counters(int64_t n) {
+    if (!use_merged_levels()) return 0;
+    int64_t c = 0;
+    for (int64_t h = kDiag; h <= kMergedMax && h < n; h *= 2) c += 2 * level_pairs(n, h);
+    return c;
+}
+// W of the merged levels: one wld x wcols matrix (ld = wld), level h in columns of its own.
+void merged_w_dims(int64_t n, int64_t *wld, int64_t *wcols) {
+    *wld = 0;
+    *wcols = 0;
+    if (!use_merged_levels()) return;
+    for (int64_t h = kDiag; h <= kMergedMax && h < n; h *= 2) {
+        *wld = h;
+        *wcols += level_pairs(n, h) * h;
+    }
+}
 
 // Workspace: T planes (3), X planes (3), R plane, W planes (3; single matrix: at the
 // positions of the B blocks of T; batch: the compact h x P*h level layout), each a group of
 // `batch` planes, then the ready counters of the single-launch schedule, then one growth
-// flag per diagonal block of every matrix.
+// flag per diagonal block of every matrix, then the dependency counters of the merged
+// low levels of every matrix, then their two W planes (hi, mid) per matrix.
 Layout layout(int64_t n, int64_t batch = 1) {
     Layout L{};
     L.ldp = round_up(std::max<int64_t>(n, 1), 64);
@@ -103,7 +129,12 @@ Layout layout(int64_t n, int64_t batch = 1) {
     L.off_w = L.off_r + g;
     L.off_f = L.off_w + 3 * g;
     L.off_g = L.off_f + al256(tc::graph_flag_bytes(n));
-    L.total = L.off_g + al256((size_t)((n + kDiag - 1) / kDiag) * (size_t)batch * sizeof(int));
+    L.off_c = L.off_g + al256((size_t)((n + kDiag - 1) / kDiag) * (size_t)batch * sizeof(int));
+    L.off_m = L.off_c + al256((size_t)merged_counters(n) * (size_t)batch * sizeof(int));
+    int64_t wld = 0, wcols = 0;
+    merged_w_dims(n, &wld, &wcols);
+    L.mplane = al256((size_t)wld * (size_t)wcols * 2);
+    L.total = L.off_m + 2 * L.mplane * (size_t)batch;
     return L;
 }
 
@@ -153,8 +184,11 @@ int level_tile_n(int64_t h) {
 struct Plan {
     tc::Tile *d_tiles = nullptr;
     int *d_off = nullptr;
-    std::vector<Launch> w, x21;   // per tc level
+    std::vector<Launch> w, x21;   // per tc level (the levels after the merged ones)
     Launch res{}, upd{};
+    Launch lvl{};                 // merged low levels (MODE_LVL), if merged_levels > 0
+    int merged_levels = 0;        // h = 256 .. 256 * 2^(merged_levels - 1)
+    int64_t wld = 0, wcols = 0;   // W layout of the merged levels: wld x wcols, ld = wld
 };
 
 // Schedule of the tensor-core products: "levels" (default) launches one persistent kernel
@@ -167,6 +201,19 @@ bool use_graph_schedule() {
         return e && std::strcmp(e, "graph") == 0;
     }();
     return g;
+}
+
+// "merged" (TRI_MIXED_SCHEDULE=merged): the low levels (h <= kMergedMax) share one
+// dependency-ordered launch (MODE_LVL); by default every level has launches of its own.
+// Measured at n = 8192: 1.420 ms per step merged against 1.404 ms per level (with
+// programmatic dependent launch the per-level boundaries cost little, and the merged
+// tiles wait on their pairs).
+bool use_merged_levels() {
+    static const bool m = [] {
+        const char *e = std::getenv("TRI_MIXED_SCHEDULE");
+        return e && std::strcmp(e, "merged") == 0;
+    }();
+    return m;
 }
 
 std::mutex g_plan_mu;
@@ -208,7 +255,113 @@ tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64
         if (vec) vec->push_back(l);
         else *one = l;
     };
-    for (int64_t h = kDiag; h < n; h *= 2) {
+    // Merged low levels (three-term recipe): W and X21 tiles of h = 256 .. kMergedMax in one
+    // launch.  Each tile waits on the counters of the tiles that write its operands:
+    //   W(h, q)    reads X_A, the inverse of [a0, a0 + h): complete once the X21 tiles of
+    //              pair 2q at level h / 2 are (they waited on everything below them);
+    //   X21(h, q)  reads W(h, q) and X_C, the inverse of [c0, c0 + hc): complete once the
+    //              X21 tiles of the largest lower level's pair starting at c0 are.
+    // Each level's W has its own columns of one wld x wcols matrix (ld = wld) in the W planes.
+    const bool merged = use_merged_levels() && !direct && n > kDiag;
+    int64_t hnext = kDiag;   // first level with launches of its own
+    if (merged) {
+        std::vector<int64_t> hs, coff, pbase;
+        int64_t cols = 0, pb = 0;
+        for (int64_t h = kDiag; h <= kMergedMax && h < n; h *= 2) {
+            hs.push_back(h);
+            coff.push_back(cols);
+            pbase.push_back(pb);
+            cols += level_pairs(n, h) * h;
+            pb += level_pairs(n, h);
+        }
+        hnext = hs.back() * 2;
+        p.merged_levels = (int)hs.size();
+        merged_w_dims(n, &p.wld, &p.wcols);
+        const int ncnt = (int)(2 * pb);
+        auto widx = [&](size_t l, int64_t q) { return (int)(2 * (pbase[l] + q)); };
+        auto xidx = [&](size_t l, int64_t q) { return (int)(2 * (pbase[l] + q) + 1); };
+        constexpr int64_t bnl = 128;
+        // pass 0 counts the tiles behind every counter, pass 1 emits the tiles with waits
+        std::vector<int> count(ncnt, 0);
+        std::vector<tc::Tile> lt;
+        std::vector<int> grp;
+        double fl = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (size_t l = 0; l < hs.size(); ++l) {
+                const int64_t h = hs[l], P = level_pairs(n, h);
+                for (int64_t q = 0; q < P; ++q) {
+                    const int64_t a0 = q * 2 * h, c0 = a0 + h, hc = std::min(h, n - c0);
+                    int xa = -1, xc = -1;   // counters of X_A and X_C (-1: complete before the launch)
+                    if (l > 0) xa = xidx(l - 1, 2 * q);
+                    for (size_t m = l; m-- > 0;)
+                        if (c0 + hs[m] < n) {
+                            xc = xidx(m, c0 / (2 * hs[m]));
+                            break;
+                        }
+                    if (pass == 1) fl += 3.0 * ((double)hc * h * (h + 1) + (double)h * hc * (hc + 1));
+                    for (int64_t tn = 0; tn < h / bnl; ++tn)
+                        for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
+                            if (pass == 0) {
+                                ++count[widx(l, q)];
+                                continue;
+                            }
+                            tc::Tile t{(int)(c0 + tm * tc::BM), (int)a0, (int)a0, (int)(a0 + tn * bnl),
+                                       (int)(tn * bnl / tc::BK), (int)(h / tc::BK), (int)(tm * tc::BM),
+                                       (int)(coff[l] + q * h + tn * bnl)};
+                            t.kind = 0;
+                            t.pub = widx(l, q);
+                            if (xa >= 0) {
+                                t.wait0 = xa;
+                                t.need0 = tc::EPI_WARPS * count[xa];
+                            }
+                            lt.push_back(t);
+                            grp.push_back((int)(2 * l));
+                        }
+                    for (int64_t tm = 0; tm < cdiv(hc, tc::BM); ++tm) {
+                        const int64_t kend = std::min((tm + 1) * tc::BM, hc);
+                        for (int64_t tn = 0; tn < h / bnl; ++tn) {
+                            if (pass == 0) {
+                                ++count[xidx(l, q)];
+                                continue;
+                            }
+                            tc::Tile t{(int)(c0 + tm * tc::BM), (int)c0, 0, (int)(coff[l] + q * h + tn * bnl), 0,
+                                       (int)cdiv(kend, tc::BK), (int)(c0 + tm * tc::BM), (int)(a0 + tn * bnl)};
+                            t.kind = 1;
+                            t.pub = xidx(l, q);
+                            t.wait0 = widx(l, q);
+                            t.need0 = tc::EPI_WARPS * count[widx(l, q)];
+                            if (xc >= 0) {
+                                t.wait1 = xc;
+                                t.need1 = tc::EPI_WARPS * count[xc];
+                            }
+                            lt.push_back(t);
+                            grp.push_back((int)(2 * l + 1));
+                        }
+                    }
+                }
+            }
+        }
+        // replicate over the batch: matrix b's tiles use its own counters
+        const size_t one = lt.size();
+        for (int64_t b = 1; b < batch; ++b)
+            for (size_t i = 0; i < one; ++i) {
+                tc::Tile t = lt[i];
+                t.b = (int)b;
+                const int o = (int)b * ncnt;
+                t.pub += o;
+                if (t.wait0 >= 0) t.wait0 += o;
+                if (t.wait1 >= 0) t.wait1 += o;
+                lt.push_back(t);
+                grp.push_back(grp[i]);
+            }
+        std::vector<int> o;
+        // one CTA per SM at most: a tile waits on tiles of other CTAs, all resident
+        const int ctas = lt.empty() ? 0 : tc::schedule_lpt_groups(lt, grp, 3, sm_count, o);
+        p.lvl = Launch{(int)v.size(), ctas, (int)offs.size(), fl * (double)batch, (int)bnl, false};
+        v.insert(v.end(), lt.begin(), lt.end());
+        for (int x : o) offs.push_back(x);
+    }
+    for (int64_t h = hnext; h < n; h *= 2) {
         const int64_t P = level_pairs(n, h);
         const int bn = level_tile_n(h);   // divides h (h is 256 * 2^s)
         // full-width three-term level products may run on CTA pairs (256-row tiles)
@@ -325,6 +478,11 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
                           : build_plan(c.device, c.sm_count, c.pairs ? tc::pair_lists(c) : 0, c.pairs, n, batch,
                                        c.recipe, &plan);
     if (st != TRI_OK) return st;
+    // dependency counters of the merged low levels start at zero
+    int *cnt = (int *)(base + L.off_c);
+    if (plan && plan->merged_levels > 0 &&
+        cudaMemsetAsync(cnt, 0, (size_t)merged_counters(n) * (size_t)batch * sizeof(int), c.stream) != cudaSuccess)
+        return TRI_ERR_CUDA;
 
     // 1. T planes of the off-diagonal part (side stream), concurrently with
     // 2.+3. the FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
@@ -379,22 +537,53 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     static const char *const kXName[] = {"tc_gemm:x21:256", "tc_gemm:x21:512", "tc_gemm:x21:1024",
                                          "tc_gemm:x21:2048", "tc_gemm:x21:4096", "tc_gemm:x21:8192",
                                          "tc_gemm:x21:16384", "tc_gemm:x21"};
+    int64_t hfirst = kDiag;
+    if (plan->merged_levels > 0) {
+        // 4a. the low levels in one launch: W tiles (targets ew) and X21 tiles (ex)
+        static const char *const kLvlName = "tc_gemm:lvl";
+        // the merged levels' W planes: wld x wcols each, mplane bytes per matrix
+        const int64_t ms = (int64_t)(L.mplane / 2);
+        __nv_bfloat16 *M0 = (__nv_bfloat16 *)(base + L.off_m), *M1 = M0 + ms * batch;
+        auto plm = [&](const __nv_bfloat16 *p) {
+            tc::Plane q{p, plan->wld, plan->wcols, plan->wld};
+            q.batch = batch;
+            q.bstride = ms;
+            return q;
+        };
+        const tc::Plane la[4] = {tp[0], tp[1], xp[0], xp[1]};
+        const tc::Plane lb[4] = {xp[0], xp[1], plm(M0), plm(M1)};
+        tc::Epi ew{nullptr, 0, M0, M1, nullptr, plan->wld, plan->wld, plan->wcols};
+        ew.os = ms;
+        ew.cnt = cnt;
+        ew.xs = 0;
+        tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
+        ex.xs = stride;
+        ex.os = ps;
+        const Launch &ll = plan->lvl;
+        if (tc::launch_tc(c, tc::MODE_LVL, trans, unit, la, 4, lb, 4, three, plan->d_tiles + ll.first,
+                          plan->d_off + ll.off_first, ll.ctas, ew, ll.flops, kLvlName, ll.bn, false, &ex) !=
+            cudaSuccess)
+            return TRI_ERR_CUDA;
+        hfirst = kDiag << plan->merged_levels;
+    }
     int lvl = 0;
-    for (int64_t h = kDiag; h < n; h *= 2, ++lvl) {
+    for (int64_t h = hfirst; h < n; h *= 2, ++lvl) {
         const int64_t P = level_pairs(n, h);
+        int name = 0;   // trace name index: log2(h / 256)
+        while ((kDiag << name) < h && name < 7) ++name;
         const tc::Plane wp[3] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h), pl(W[2], h, P * h, h)};
         tc::Epi ew{nullptr, 0, W[0], W[1], direct ? W[2] : nullptr, h, h, P * h};
         ew.os = ps;
         const Launch &lw = plan->w[lvl];
         if (tc::launch_tc(c, mw, trans, unit, tp, 3, xp, 3, lt, plan->d_tiles + lw.first, plan->d_off + lw.off_first,
-                          lw.ctas, ew, lw.flops, kWName[std::min(lvl, 7)], lw.bn, lw.pair) != cudaSuccess)
+                          lw.ctas, ew, lw.flops, kWName[name], lw.bn, lw.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
         tc::Epi ex{a, lda, X[0], X[1], X[2], L.ldp, n, n};
         ex.xs = stride;
         ex.os = ps;
         const Launch &lx = plan->x21[lvl];
         if (tc::launch_tc(c, mx, trans, unit, xp, 3, wp, nw, lt, plan->d_tiles + lx.first, plan->d_off + lx.off_first,
-                          lx.ctas, ex, lx.flops, kXName[std::min(lvl, 7)], lx.bn, lx.pair) != cudaSuccess)
+                          lx.ctas, ex, lx.flops, kXName[name], lx.bn, lx.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
     if (direct) return TRI_OK;

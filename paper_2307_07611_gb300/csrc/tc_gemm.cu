@@ -88,14 +88,58 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
     return ctas;
 }
 
+int schedule_lpt_groups(std::vector<Tile> &tiles, const std::vector<int> &group, int terms, int ctas,
+                        std::vector<int> &offsets) {
+    const int nt = (int)tiles.size();
+    if (ctas > nt) ctas = nt;
+    if (ctas < 1) ctas = 1;
+    constexpr int kEpilogueCost = 8;   // pipeline-slot equivalents per tile (as schedule_lpt)
+    auto cost = [&](int i) { return (tiles[i].kb1 - tiles[i].kb0) * terms + kEpilogueCost; };
+    std::vector<int> order(nt);
+    for (int i = 0; i < nt; ++i) order[i] = i;
+    // by group, then longest first
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return group[x] != group[y] ? group[x] < group[y] : cost(x) > cost(y);
+    });
+    std::vector<std::pair<long long, int>> heap;
+    for (int b = 0; b < ctas; ++b) heap.push_back({0, b});
+    auto cmp = [](const std::pair<long long, int> &x, const std::pair<long long, int> &y) {
+        return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    std::vector<std::vector<int>> lists(ctas);
+    for (int i : order) {   // each CTA's list stays in group order
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto &top = heap.back();
+        lists[top.second].push_back(i);
+        top.first += cost(i);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<Tile> out;
+    out.reserve(nt);
+    offsets.assign(ctas + 1, 0);
+    for (int b = 0; b < ctas; ++b) {
+        offsets[b] = (int)out.size();
+        for (int i : lists[b]) out.push_back(tiles[i]);
+    }
+    offsets[ctas] = (int)out.size();
+    tiles.swap(out);
+    return ctas;
+}
+
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes, int na,
                       const Plane *bplanes, int nb, const Terms &terms, const Tile *d_tiles,
                       const int *d_off, int ctas, const Epi &epi, double flops,
-                      const char *trace_name, int bn, bool pair) {
+                      const char *trace_name, int bn, bool pair, const Epi *epi2) {
     if (ctas <= 0) return cudaSuccess;
-    if (na < 1 || na > 3 || nb < 1 || nb > 3 || terms.n < 1 || terms.n > 6) return cudaErrorInvalidValue;
+    const bool lvl = mode == MODE_LVL;
+    if (lvl ? (na != 4 || nb != 4 || bn != 128 || pair || !epi2 || !epi.cnt)
+            : (na < 1 || na > 3 || nb < 1 || nb > 3))
+        return cudaErrorInvalidValue;
+    if (terms.n < 1 || terms.n > 6 || (lvl && terms.n != 3)) return cudaErrorInvalidValue;
+    const Epi &e2 = epi2 ? *epi2 : epi;
     // narrow tiles are built for the level products only
-    const bool level = mode == MODE_W || mode == MODE_X21 || mode == MODE_W6 || mode == MODE_X216;
+    const bool level = mode == MODE_W || mode == MODE_X21 || mode == MODE_W6 || mode == MODE_X216 || lvl;
     if (bn != BN && !((bn == 128 || bn == 64) && level)) return cudaErrorInvalidValue;
     // CTA pairs: the products of the mixed path, full-width tiles
     if (pair && !(bn == BN && (mode == MODE_W || mode == MODE_X21 || mode == MODE_RES || mode == MODE_UPD)))
@@ -104,7 +148,7 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     Maps maps;
     memset(&maps, 0, sizeof(maps));
     const Cfg cf = cfg_for(mode);
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         const Plane &pa = aplanes[i < na ? i : 0];
         const Plane &pb = bplanes[i < nb ? i : 0];
         if (!encode_plane(&maps.a[i], pa, 64, cf.ks)) return cudaErrorInvalidValue;
@@ -113,7 +157,9 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     // Stage layout: every distinct plane the terms read (fused), or one term's pair.
     Pipe pipe{1, 1, 0, 0, 0};
     for (int j = 0; j < terms.n; ++j) {
-        if (terms.a[j] < 0 || terms.a[j] >= na || terms.b[j] < 0 || terms.b[j] >= nb) return cudaErrorInvalidValue;
+        // MODE_LVL: the X21 tiles use the W terms' planes shifted by two
+        const int ra = lvl ? na - 2 : na, rb = lvl ? nb - 2 : nb;
+        if (terms.a[j] < 0 || terms.a[j] >= ra || terms.b[j] < 0 || terms.b[j] >= rb) return cudaErrorInvalidValue;
         if (cf.fused) {
             pipe.na = std::max(pipe.na, terms.a[j] + 1);
             pipe.nb = std::max(pipe.nb, terms.b[j] + 1);
@@ -129,10 +175,10 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     TraceScope ts(c.stream, trace_name, flops, 0.0);
     if (pair) return launch_pair(c, mode, trans, unit, maps, terms, pipe, d_tiles, d_off, ctas, epi);
 #define TRI_TC_CASE_N(M, N)                                                                   \
-        if (trans) return unit ? launch_t<M, true, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)   \
-                               : launch_t<M, true, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi); \
-        return unit ? launch_t<M, false, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)             \
-                    : launch_t<M, false, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+        if (trans) return unit ? launch_t<M, true, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2)   \
+                               : launch_t<M, true, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2); \
+        return unit ? launch_t<M, false, true, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2)             \
+                    : launch_t<M, false, false, N>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2);
 #define TRI_TC_CASE(M) \
     case M:            \
         TRI_TC_CASE_N(M, BN)
@@ -146,14 +192,16 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
         TRI_TC_CASE_LEVEL(MODE_X21)
         TRI_TC_CASE_LEVEL(MODE_W6)
         TRI_TC_CASE_LEVEL(MODE_X216)
+        case MODE_LVL:
+            TRI_TC_CASE_N(MODE_LVL, 128)
         TRI_TC_CASE(MODE_RES)
         TRI_TC_CASE(MODE_UPD)
         case MODE_F32:
-            return launch_t<MODE_F32, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+            return launch_t<MODE_F32, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2);
         case MODE_GEN:
-            return launch_t<MODE_GEN, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+            return launch_t<MODE_GEN, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2);
         case MODE_GENP:
-            return launch_t<MODE_GENP, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+            return launch_t<MODE_GENP, false, false>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, e2);
         default:
             return cudaErrorInvalidValue;
     }

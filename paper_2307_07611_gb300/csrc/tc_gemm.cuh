@@ -18,9 +18,15 @@ constexpr int BK = 64;    // k-block staged per pipeline slot (one 128-byte swiz
 // One output tile: operand A rows [am, am+128) and columns ak + [kb0*64, kb1*64);
 // operand B rows bk + [kb0*64, kb1*64) and columns [bn, bn+256); output origin (om, on);
 // b: matrix of a batch (planes and outputs offset by b times their batch strides).
+// MODE_LVL only: kind 0 = a W tile, 1 = an X21 tile; before loading its operands the tile
+// waits until counter wait0 (wait1) of Epi::cnt reaches need0 (need1) (-1: no wait), and
+// after storing it adds one per epilogue warp to counter pub (-1: none).
 struct Tile {
     int am, ak, bk, bn, kb0, kb1, om, on;
     int b = 0;
+    int kind = 0;
+    int wait0 = -1, need0 = 0, wait1 = -1, need1 = 0;
+    int pub = -1;
 };
 
 // Products summed into one FP32 accumulator: sum_t A_{a[t]} * B_{b[t]}.
@@ -44,6 +50,7 @@ struct Epi {
     int64_t xs = 0, os = 0;        // batch strides (elements) of x and of the output planes
     const int *skip = nullptr;     // MODE_RES: skip_n flags per matrix of the batch; a matrix
     int skip_n = 0;                // with a flag set gets R = 0 (its Newton-Schulz step is a no-op)
+    int *cnt = nullptr;            // MODE_LVL: the dependency counters the tiles wait on / add to
 };
 
 enum Mode {
@@ -57,6 +64,10 @@ enum Mode {
                      // every 64 k (the six-term products that must reach ~2^-24)
     MODE_W6 = 7,     // MODE_W with six promoted terms; o0/o1/o2 <- hi/mid/lo  (direct recipe)
     MODE_X216 = 8,   // MODE_X21 with six promoted terms                       (direct recipe)
+    MODE_LVL = 9,    // W tiles (kind 0, as MODE_W, epilogue targets of the first Epi) and
+                     // X21 tiles (kind 1, as MODE_X21, second Epi) of several split levels in
+                     // one launch, ordered by their data dependencies (see Tile); A maps
+                     // T0 T1 X0 X1, B maps X0 X1 W0 W1, the X21 terms offset by two planes
 };
 
 // A column-major BF16 plane usable as a TMA source: rows x cols, leading dimension ld
@@ -87,10 +98,20 @@ int schedule_lpt(std::vector<Tile> &tiles, int terms, int ctas, std::vector<int>
 // products (MODE_W, MODE_X21, MODE_W6, MODE_X216).
 // pair: the list holds 256-row tiles (BN wide; MODE_W, MODE_X21, MODE_RES, MODE_UPD), each
 // computed by a cluster of two CTAs; `ctas` is twice the number of lists.
+// MODE_LVL: na = nb = 4, bn = 128, epi2 = the X21 tiles' epilogue targets; every CTA of the
+// launch must be resident at once (ctas <= SMs; one CTA per SM), since tiles wait on tiles
+// of other CTAs (waits are bounded: TRI_ERR_TIMEOUT otherwise).
 cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane *aplanes,
                       int na, const Plane *bplanes, int nb, const Terms &terms,
                       const Tile *d_tiles, const int *d_off, int ctas, const Epi &epi,
-                      double flops, const char *trace_name, int bn = BN, bool pair = false);
+                      double flops, const char *trace_name, int bn = BN, bool pair = false,
+                      const Epi *epi2 = nullptr);
+
+// Longest-first assignment like schedule_lpt, for tiles in dependency groups: group g's
+// tiles (group[i] = g of tiles[i], groups numbered in dependency order) come after every
+// tile of groups < g in each CTA's list; loads carry over from group to group.
+int schedule_lpt_groups(std::vector<Tile> &tiles, const std::vector<int> &group, int terms, int ctas,
+                        std::vector<int> &offsets);
 
 // Rows of the output tiles of a CTA-pair launch.
 constexpr int PAIR_BM = 2 * BM;

@@ -15,10 +15,10 @@ cudaError_t launch_pair(const Ctx &c, int mode, bool trans, bool unit, const Map
 #define TRI_PAIR_CASE(M)                                                                                    \
     case M:                                                                                                 \
         if (trans)                                                                                          \
-            return unit ? launch_t<M, true, true, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi) \
-                        : launch_t<M, true, false, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi); \
-        return unit ? launch_t<M, false, true, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi)    \
-                    : launch_t<M, false, false, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi);
+            return unit ? launch_t<M, true, true, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, epi) \
+                        : launch_t<M, true, false, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, epi); \
+        return unit ? launch_t<M, false, true, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, epi)    \
+                    : launch_t<M, false, false, BN, true>(c, maps, terms, pipe, d_tiles, d_off, ctas, epi, epi);
     switch (mode) {
         TRI_PAIR_CASE(MODE_W)
         TRI_PAIR_CASE(MODE_X21)

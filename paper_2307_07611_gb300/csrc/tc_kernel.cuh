@@ -53,8 +53,8 @@ namespace triinv {
 namespace tc {
 
 struct Maps {
-    CUtensorMap a[3];
-    CUtensorMap b[3];
+    CUtensorMap a[4];
+    CUtensorMap b[4];
 };
 
 // Pipeline geometry per mode.
@@ -200,6 +200,37 @@ __device__ __forceinline__ void store_upd16(const Epi &ep, int64_t xb, int64_t g
     }
 }
 
+// Dependency counters of MODE_LVL (global memory, written by other CTAs of the launch).
+__device__ __forceinline__ int dep_ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dep_red_release_add(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dep_fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Bounded wait until *c >= need.  False if the CTA is aborting or the deadline passed (then
+// it raises the abort flag and the device timeout word).
+__device__ __forceinline__ bool dep_wait(const int *c, int need, volatile int *abort_flag, int *gtimeout) {
+    if (dep_ld_acquire(c) >= need) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        __nanosleep(64);
+        if (dep_ld_acquire(c) >= need) return true;
+        if ((i & 15) == 0) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > kWaitLimitNs) {
+                *abort_flag = 1;
+                atomicExch(gtimeout, 1);
+                return false;
+            }
+        }
+    }
+}
+
 // Drain wait after an abort: gives up at `deadline` (globaltimer ns).
 __device__ __forceinline__ void mbar_wait_drain_until(uint32_t bar, uint32_t parity, uint64_t deadline) {
     while (!mbar_try_wait(bar, parity)) {
@@ -215,7 +246,7 @@ template <int MODE, bool TRANS, bool UNIT, int BNT, bool PAIR = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe pipe,
                const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
-               int *gtimeout) {
+               const Epi ep2, int *gtimeout) {
     constexpr bool PROMOTE = (MODE == MODE_RES || MODE == MODE_GENP || MODE == MODE_W6 || MODE == MODE_X216);
     constexpr Cfg CF = cfg_for(MODE);
     constexpr int KS = CF.ks;
@@ -311,7 +342,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0 && lane == 0) {
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 4; ++i) {
             prefetch_map(&maps.a[i]);
             prefetch_map(&maps.b[i]);
         }
@@ -361,6 +392,17 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
             for (int t = t_begin; t < t_end && ok; ++t) {
                 const Tile tl = tiles[t];
                 const int cb = chunk_blocks(tl);
+                // MODE_LVL: X21 tiles read the X21 planes' maps (two further on)
+                const int toff = (MODE == MODE_LVL && tl.kind) ? 2 : 0;
+                if (MODE == MODE_LVL && (tl.wait0 >= 0 || tl.wait1 >= 0)) {
+                    // operands written by other CTAs of this launch (generic-proxy stores,
+                    // published with release adds): acquire, then order the async-proxy reads
+                    if (tl.wait0 >= 0) ok = dep_wait(ep.cnt + tl.wait0, tl.need0, abort_flag, gtimeout);
+                    if (ok && tl.wait1 >= 0) ok = dep_wait(ep.cnt + tl.wait1, tl.need1, abort_flag, gtimeout);
+                    if (!ok) break;
+                    __threadfence();
+                    dep_fence_proxy_async_global();
+                }
                 for (int c0 = tl.kb0; c0 < tl.kb1 && ok; c0 += cb) {
                     const int c1 = min(c0 + cb, tl.kb1);
                     // fused: one pass with every plane; else one pass per term (smallest first)
@@ -373,7 +415,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                                 }
                                 const int k = kb * BK + hk * KS;
                                 if (CF.fused) load_stage(st, full_bar(s), tl, k, 0, 0, pipe.na, pipe.nb);
-                                else load_stage(st, full_bar(s), tl, k, terms.a[j], terms.b[j], 1, 1);
+                                else load_stage(st, full_bar(s), tl, k, terms.a[j] + toff, terms.b[j] + toff, 1, 1);
                                 ++it;
                                 if (++s == STAGES) {
                                     s = 0;
@@ -522,6 +564,23 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                             for (int i = 0; i < 16; ++i) xv[i] = xn[i];
                         }
                     }
+                } else if (MODE == MODE_LVL) {
+                    if (tl.kind) {
+                        const int64_t xb2 = (int64_t)tl.b * ep2.xs, ob2 = (int64_t)tl.b * ep2.os;
+#pragma unroll 1
+                        for (int q = 0; q < BNT / 16; ++q) {
+                            uint32_t r[8];
+                            tmem_ld8(taddr + q * 8, r);
+                            epilogue_cols<MODE_X21, TRANS, UNIT, 8>(ep2, xb2, ob2, gm, gcol0 + q * 8, r);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int q = 0; q < BNT / 16; ++q) {
+                            uint32_t r[8];
+                            tmem_ld8(taddr + q * 8, r);
+                            epilogue_cols<MODE_W, TRANS, UNIT, 8>(ep, xb, ob, gm, gcol0 + q * 8, r);
+                        }
+                    }
                 } else {
 #pragma unroll 1
                     for (int q = 0; q < BNT / 16; ++q) {
@@ -536,6 +595,14 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                     if constexpr (PAIR) mbar_arrive_cluster(tempty_rel0 + 8u * a);
                     else mbar_arrive(tempty_bar(a));
                 }
+            }
+            if (MODE == MODE_LVL && ok && tl.pub >= 0) {
+                // Publish this warp's part of the tile: its generic-proxy stores visible at
+                // GPU scope and to later async-proxy (TMA) reads, then one release add.
+                dep_fence_proxy_async_global();
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) dep_red_release_add(ep.cnt + tl.pub, 1);
             }
             if (PROMOTE && ok) {
                 // a matrix whose diagonal block needed the FP64 fallback skips its step
@@ -580,7 +647,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
 // Launch of `ctas` persistent CTAs (PAIR: ctas / 2 clusters of two).
 template <int MODE, bool TRANS, bool UNIT, int BNT = BN, bool PAIR = false>
 cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const Pipe &pipe, const Tile *d_tiles,
-                     const int *d_off, int ctas, const Epi &epi) {
+                     const int *d_off, int ctas, const Epi &epi, const Epi &epi2) {
     auto kern = tc_gemm_kernel<MODE, TRANS, UNIT, BNT, PAIR>;
     static bool attr_set[64] = {};
     if (!attr_set[c.device]) {
@@ -606,7 +673,7 @@ cudaError_t launch_t(const Ctx &c, const Maps &maps, const Terms &terms, const P
         attr[1].val.clusterDim.z = 1;
         cfg.numAttrs = 2;
     }
-    return cudaLaunchKernelEx(&cfg, kern, maps, terms, pipe, d_tiles, d_off, epi, c.timeout);
+    return cudaLaunchKernelEx(&cfg, kern, maps, terms, pipe, d_tiles, d_off, epi, epi2, c.timeout);
 }
 
 }  // namespace

@@ -179,3 +179,39 @@ def test_mixed_graph_schedule_same_results(lib):
                        cwd=root, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
     assert " passed" in r.stdout
+
+
+def test_mixed_merged_levels_bit_identical_to_per_level_launches(lib, tmp_path):
+    """Every split level runs by default in launches of its own; TRI_MIXED_SCHEDULE=merged
+    (read once per process) runs the low levels (h = 256 .. 1024) as one launch whose
+    tiles wait on the dependency counters of the pairs they read.  Both run the same
+    products in the same order, so the inverses must be bit-identical: the merged result
+    is computed in a child process and compared."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cases = [(700, 1, True, False), (1537, 2, True, False), (2048, 3, False, True), (3000, 4, True, False)]
+    child = (
+        "import sys, numpy as np, torch\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2307_07611_gb300 import inputs, lib\n"
+        "from tests._gpu import run_tri_inv\n"
+        "lib.load()\n"
+        "for n, seed, lower, unit in %r:\n"
+        "    t = inputs.tri_lower(n, seed=seed, law='normal', dtype=np.float32).astype(np.float64)\n"
+        "    t = t if lower else t.T.copy()\n"
+        "    x, st = run_tri_inv(lib, torch, t, lower=lower, unit=unit, dtype='f32', mixed=True)\n"
+        "    assert st == lib.TRI_OK\n"
+        "    np.save(%r + '/x%%d.npy' %% n, x)\n" % (root, cases, str(tmp_path)))
+    env = dict(os.environ, TRI_MIXED_SCHEDULE="merged")
+    r = subprocess.run([sys.executable, "-c", child], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-3000:]
+    for n, seed, lower, unit in cases:
+        t = inputs.tri_lower(n, seed=seed, law="normal", dtype=np.float32).astype(np.float64)
+        t = t if lower else t.T.copy()
+        x, st = run_tri_inv(lib, torch, t, lower=lower, unit=unit, dtype="f32", mixed=True)
+        assert st == lib.TRI_OK and lib.tri_get_info()[0] == lib.TRI_OK
+        assert np.array_equal(x, np.load(str(tmp_path / ("x%d.npy" % n)))), n
+        assert rel_max_err(x, oracle.tri_inv(t, lower=lower, unit=unit)) <= tol(n)
