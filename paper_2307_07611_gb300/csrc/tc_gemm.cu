@@ -147,7 +147,7 @@ cudaError_t launch_tc(const Ctx &c, int mode, bool trans, bool unit, const Plane
     const int bcols = pair ? bn / 2 : bn;   // B columns one CTA stages
     Maps maps;
     memset(&maps, 0, sizeof(maps));
-    const Cfg cf = cfg_for(mode);
+    const Cfg cf = cfg_for(mode, bn);
     for (int i = 0; i < 4; ++i) {
         const Plane &pa = aplanes[i < na ? i : 0];
         const Plane &pb = bplanes[i < nb ? i : 0];

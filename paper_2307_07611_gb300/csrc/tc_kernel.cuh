@@ -69,16 +69,21 @@ struct Maps {
 //            term loses up to one unit in the last place of the partial sum; the chunk
 //            length bounds that loss.
 // R = I - T X and the general six-term products read 3 + 3 planes: fused 32-wide stages
-// (72 KB, 3 deep) halve their L2 traffic; one-term and three-term products keep 64-wide
-// per-term stages (48 KB, 4 deep), which measured faster for them.
+// (72 KB, 3 deep) halve their L2 traffic.  The three-term level products with 64- or
+// 128-wide output tiles take fused 64-wide stages (both planes of each operand, 12 MMAs
+// per stage; 48 / 64 KB, 4 / 3 deep); with 256-wide tiles such a stage is 96 KB and only
+// two fit, so they, the update and the other products keep 64-wide per-term stages
+// (48 KB, 4 deep).  Each choice measured fastest at n = 8192 (more tensor work per stage
+// helps while the ring stays at least three deep).
 struct Cfg {
     int ks;
     bool fused;
     int promote;
 };
-__host__ __device__ constexpr Cfg cfg_for(int mode) {
+__host__ __device__ constexpr Cfg cfg_for(int mode, int bn = BN) {
     return (mode == MODE_RES || mode == MODE_GENP || mode == MODE_W6 || mode == MODE_X216) ? Cfg{32, true, 1}
-                                                                                         : Cfg{64, false, 0};
+           : ((mode == MODE_W || mode == MODE_X21 || mode == MODE_LVL) && bn <= 128) ? Cfg{64, true, 0}
+                                                                                  : Cfg{64, false, 0};
 }
 
 constexpr int STAGE_BUDGET = 216 * 1024;
@@ -248,7 +253,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                const Tile *__restrict__ tiles, const int *__restrict__ cta_off, const Epi ep,
                const Epi ep2, int *gtimeout) {
     constexpr bool PROMOTE = (MODE == MODE_RES || MODE == MODE_GENP || MODE == MODE_W6 || MODE == MODE_X216);
-    constexpr Cfg CF = cfg_for(MODE);
+    constexpr Cfg CF = cfg_for(MODE, BNT);
     constexpr int KS = CF.ks;
     constexpr int BNL = PAIR ? BNT / 2 : BNT;   // B columns this CTA stages
     constexpr int A_TILE = BM * KS * 2, B_TILE = BNL * KS * 2;
@@ -414,7 +419,7 @@ tc_gemm_kernel(const __grid_constant__ Maps maps, const Terms terms, const Pipe 
                                     break;
                                 }
                                 const int k = kb * BK + hk * KS;
-                                if (CF.fused) load_stage(st, full_bar(s), tl, k, 0, 0, pipe.na, pipe.nb);
+                                if (CF.fused) load_stage(st, full_bar(s), tl, k, toff, toff, pipe.na, pipe.nb);
                                 else load_stage(st, full_bar(s), tl, k, terms.a[j] + toff, terms.b[j] + toff, 1, 1);
                                 ++it;
                                 if (++s == STAGES) {
