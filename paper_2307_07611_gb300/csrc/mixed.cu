@@ -41,7 +41,7 @@ namespace triinv {
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
                                 __nv_bfloat16 *p2, int64_t ldp, bool skip_diag, int64_t batch, int64_t as_,
-                                int64_t ps);
+                                int64_t ps, int lmin = 0, int lmax = 62);
 cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda,
                                __nv_bfloat16 *p0, __nv_bfloat16 *p1, __nv_bfloat16 *p2, int64_t ldp,
                                __nv_bfloat16 *q0, __nv_bfloat16 *q1, __nv_bfloat16 *q2, int64_t batch,
@@ -51,7 +51,7 @@ cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, f
 // (fork / join through events, so the pair also works inside stream capture).
 struct SideStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
 std::mutex g_side_mu;
 SideStream g_side[64];
@@ -64,6 +64,7 @@ bool side_stream(int dev, SideStream **out) {
         if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess) return false;
         if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return false;
         if (cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&ss.join2, cudaEventDisableTiming) != cudaSuccess) return false;
     }
     *out = &ss;
     return true;
@@ -201,6 +202,18 @@ bool use_graph_schedule() {
         return e && std::strcmp(e, "graph") == 0;
     }();
     return g;
+}
+
+// Split levels whose B blocks are split beside the diagonal-block kernel (the rest follow
+// on the side stream while those levels run).  TRI_SPLIT_HEAD_LEVELS (>= 1) overrides
+// the default of 2 (h = 256 and 512), read once; a large value splits all of T first.
+int split_head_levels() {
+    static const int v = [] {
+        const char *e = std::getenv("TRI_SPLIT_HEAD_LEVELS");
+        const int x = e ? std::atoi(e) : 2;
+        return x >= 1 ? x : 2;
+    }();
+    return v;
 }
 
 // "merged" (TRI_MIXED_SCHEDULE=merged): the low levels (h <= kMergedMax) share one
@@ -488,6 +501,11 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     // 2.+3. the FP32 diagonal blocks of 256, each inverted in shared memory by one CTA (CRIT
     //       leaves of 32 and the split levels 32, 64, 128), which also writes the T and X
     //       planes of its block.  The two touch disjoint parts of T.
+    //    Only the B blocks of the first kHeadLevels split levels are split beside the
+    //    diagonal blocks; the rest (most of T) follows on the side stream while those
+    //    levels run, and the main stream waits for it before the next level.  (The split
+    //    runs at full HBM bandwidth; beside it the latency-bound diagonal-block kernel
+    //    took 90 us against 64 us alone.)
     SideStream *ss = nullptr;
     std::unique_lock<std::mutex> side_lock(g_side_mu);
     if (!side_stream(c.device, &ss)) return TRI_ERR_CUDA;
@@ -503,14 +521,34 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         return TRI_ERR_CUDA;
     Ctx cs = c;
     cs.stream = ss->s;
-    if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps) !=
-        cudaSuccess)
+    const int kHeadLevels = split_head_levels();
+    int nlevels = 0;   // split levels h = 256 * 2^l < n
+    for (int64_t h = kDiag; h < n; h *= 2) ++nlevels;
+    const bool rest = nlevels > kHeadLevels;   // B blocks left for the side stream
+    if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps, 0,
+                            rest ? kHeadLevels - 1 : 62) != cudaSuccess)
         return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
-    side_lock.unlock();
+    if (rest) {
+        if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps,
+                                kHeadLevels, 62) != cudaSuccess ||
+            cudaEventRecord(ss->join2, ss->s) != cudaSuccess)
+            return TRI_ERR_CUDA;
+    }
+    // the main stream's wait for the rest of the planes (before level kHeadLevels)
+    bool rest_joined = !rest;
+    auto join_rest = [&]() -> bool {
+        if (rest_joined) return true;
+        rest_joined = true;
+        const bool ok = cudaStreamWaitEvent(c.stream, ss->join2, 0) == cudaSuccess;
+        side_lock.unlock();
+        return ok;
+    };
+    if (!rest) side_lock.unlock();
 
     if (graph) {
+        if (!join_rest()) return TRI_ERR_CUDA;
         // 4. + 5. as one dependency-driven launch (W planes at the B-block positions)
         int *flags = (int *)(base + L.off_f);
         tc::GEpi ep{a, lda, X[0], X[1], X[2], W[0], W[1], R[0], L.ldp, n, flags,
@@ -539,6 +577,7 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
                                          "tc_gemm:x21:16384", "tc_gemm:x21"};
     int64_t hfirst = kDiag;
     if (plan->merged_levels > 0) {
+        if (!join_rest()) return TRI_ERR_CUDA;
         // 4a. the low levels in one launch: W tiles (targets ew) and X21 tiles (ex)
         static const char *const kLvlName = "tc_gemm:lvl";
         // the merged levels' W planes: wld x wcols each, mplane bytes per matrix
@@ -571,6 +610,7 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         const int64_t P = level_pairs(n, h);
         int name = 0;   // trace name index: log2(h / 256)
         while ((kDiag << name) < h && name < 7) ++name;
+        if (name >= kHeadLevels && !join_rest()) return TRI_ERR_CUDA;
         const tc::Plane wp[3] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h), pl(W[2], h, P * h, h)};
         tc::Epi ew{nullptr, 0, W[0], W[1], direct ? W[2] : nullptr, h, h, P * h};
         ew.os = ps;
@@ -586,6 +626,7 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
                           lx.ctas, ex, lx.flops, kXName[name], lx.bn, lx.pair) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
+    if (!join_rest()) return TRI_ERR_CUDA;
     if (direct) return TRI_OK;
     // 5. Newton-Schulz: R = I - T X, then X += X R
     tc::Epi er{nullptr, 0, R[0], nullptr, nullptr, L.ldp, n, n};

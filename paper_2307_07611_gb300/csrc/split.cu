@@ -28,7 +28,9 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 
 // One 64 x 64 tile per CTA.  DIAG_ONLY: blockIdx.z is the diagonal 256-block and
 // (blockIdx.x, blockIdx.y) the tile inside it; otherwise (blockIdx.x, blockIdx.y) is the
 // tile of the whole matrix, blockIdx.z the matrix of a batch (source as_ and planes ps
-// elements apart), and tiles that no product reads return at once.
+// elements apart), and tiles that no product reads return at once, as do tiles outside
+// the split levels lmin .. lmax: an off-diagonal 256-block (I, J) is the B block of split
+// half-size 256 * 2^l with l the highest set bit of I XOR J (diagonal blocks: level 0).
 // Thread t owns rows (2*(t%32), 2*(t%32)+1) of the tile and columns t/32 + 8*c, so a warp
 // stores 64 consecutive rows (128 bytes per plane) per column.
 template <bool TRANS, bool UNIT, bool DIAG_ONLY>
@@ -36,7 +38,8 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
                                                     __nv_bfloat16 *__restrict__ p0,
                                                     __nv_bfloat16 *__restrict__ p1,
                                                     __nv_bfloat16 *__restrict__ p2, int64_t ldp,
-                                                    bool skip_diag, int64_t as_, int64_t ps) {
+                                                    bool skip_diag, int64_t as_, int64_t ps, int lmin,
+                                                    int lmax) {
     int64_t i0, j0;
     if (!DIAG_ONLY && blockIdx.z) {
         a += (int64_t)blockIdx.z * as_;
@@ -53,6 +56,8 @@ __global__ void __launch_bounds__(256) split_kernel(const float *__restrict__ a,
         const bool diag_block = (i0 / 256) == (j0 / 256);
         if (!diag_block && j0 > i0) return;        // strictly upper block: never read
         if (diag_block && skip_diag) return;       // written by the diagonal-block kernel
+        const int lv = diag_block ? 0 : 31 - __clz((unsigned)((i0 / 256) ^ (j0 / 256)));
+        if (lv < lmin || lv > lmax) return;
     }
     if (i0 >= n || j0 >= n) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -207,7 +212,7 @@ cudaError_t launch_split_rect(const Ctx &c, const float *a, int64_t lds, int64_t
 cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_only, int64_t n,
                                 const float *a, int64_t lda, __nv_bfloat16 *p0, __nv_bfloat16 *p1,
                                 __nv_bfloat16 *p2, int64_t ldp, bool skip_diag, int64_t batch,
-                                int64_t as_, int64_t ps) {
+                                int64_t as_, int64_t ps, int lmin, int lmax) {
     const int64_t t = (n + TS - 1) / TS;
     if (t <= 0 || batch <= 0) return cudaSuccess;
     if (batch > 65535 || (diag_only && batch > 1)) return cudaErrorInvalidValue;
@@ -216,7 +221,7 @@ cudaError_t launch_split_planes(const Ctx &c, bool trans, bool unit, bool diag_o
     const double elems = (diag_only ? (double)n * 256.0 : (double)n * n / 2.0) * (double)batch;
     TraceScope ts(c.stream, diag_only ? "split_diag" : "split_t", 0.0, elems * (4.0 + 6.0));
 #define TRI_SPLIT(TR, UN, DO) \
-    split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp, skip_diag, as_, ps)
+    split_kernel<TR, UN, DO><<<grid, 256, 0, c.stream>>>(a, lda, n, p0, p1, p2, ldp, skip_diag, as_, ps, lmin, lmax)
     if (diag_only) {
         if (trans) { if (unit) TRI_SPLIT(true, true, true); else TRI_SPLIT(true, false, true); }
         else { if (unit) TRI_SPLIT(false, true, true); else TRI_SPLIT(false, false, true); }
