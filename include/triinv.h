@@ -334,7 +334,11 @@ TRI_API tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void
  * same split, Section 3 / Algorithm COMBRIT with beta = 2): the referenced triangle is
  * copied to the device in 256-column panels (one 2-D copy each, about half of the n x n
  * matrix), inverted with `dtype` on `stream`, and copied back the same way; the other
- * triangle of the host matrix is neither read nor written.  Device memory for the matrix
+ * triangle of the host matrix is neither read nor written.  TRI_F32_MIXED sends the
+ * triangle instead as the blocks of the recursive split (the 256 x 256 diagonal squares,
+ * then each level's off-diagonal blocks), on a copy stream of the library's, in the order
+ * the inverse first reads them: the inverse starts on the first blocks while the rest is
+ * in flight (the result is the same).  Device memory for the matrix
  * and the workspace comes from the stream-ordered pool and is released before return.
  * Synchronises `stream` before returning (the host matrix holds the result on return).
  * Page-locked host memory gives full link bandwidth; pageable memory also works.

@@ -345,6 +345,56 @@ static int64_t host_panel_copies(bool upper, int64_t n, uint8_t *dev, int64_t ld
     return bytes;
 }
 
+// Mixed path: the referenced triangle travels in the order the inverse first reads it, on a
+// copy stream of its own: the diagonal 256-blocks and the B blocks of the first split
+// levels, then the B blocks of each further level (the blocks of the recursive split tile
+// the triangle).  An event after each part lets the inverse start on the first parts while
+// the rest is still in flight (run_mixed_fed).
+struct HostFeed {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t ready[26] = {};
+};
+std::mutex g_feed_mu;
+HostFeed g_feed[64];
+
+static int64_t host_block_copies(bool upper, int64_t n, uint8_t *dev, int64_t ldd, uint8_t *host, int64_t ldh,
+                                 size_t es, HostFeed &f, int *parts, cudaError_t *err) {
+    constexpr int64_t kDiagB = 256;
+    const int head = mixed_head_levels();
+    int64_t bytes = 0;
+    // lower-view block rows [r0, r0 + rows) x columns [c0, c0 + cols); stored transposed
+    // for an upper matrix
+    auto copy = [&](int64_t r0, int64_t rows, int64_t c0, int64_t cols) {
+        if (*err != cudaSuccess || rows <= 0 || cols <= 0) return;
+        if (upper) {
+            std::swap(r0, c0);
+            std::swap(rows, cols);
+        }
+        *err = cudaMemcpy2DAsync(dev + ((size_t)c0 * ldd + r0) * es, ldd * es, host + ((size_t)c0 * ldh + r0) * es,
+                                 ldh * es, rows * es, cols, cudaMemcpyHostToDevice, f.s);
+        bytes += rows * cols * (int64_t)es;
+    };
+    auto level_blocks = [&](int64_t h) {
+        for (int64_t q = 0; q < level_pairs(n, h); ++q) {
+            const int64_t a0 = 2 * q * h, c0 = a0 + h;
+            copy(c0, std::min(h, n - c0), a0, h);
+        }
+    };
+    int k = 0;
+    for (int64_t d0 = 0; d0 < n; d0 += kDiagB) copy(d0, std::min(kDiagB, n - d0), d0, std::min(kDiagB, n - d0));
+    int l = 0;
+    int64_t h = kDiagB;
+    for (; h < n && l < head; h *= 2, ++l) level_blocks(h);
+    if (*err == cudaSuccess) *err = cudaEventRecord(f.ready[k++], f.s);
+    for (; h < n && k < 26; h *= 2) {
+        level_blocks(h);
+        if (*err == cudaSuccess) *err = cudaEventRecord(f.ready[k++], f.s);
+    }
+    *parts = k;
+    return bytes;
+}
+
 tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda, tri_dtype dtype,
                         void *stream, int64_t *bytes_moved) {
     if (bytes_moved) *bytes_moved = 0;
@@ -366,11 +416,41 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
     }
     cudaError_t e = cudaSuccess;
     const bool upper = uplo == TRI_UPPER;
-    int64_t moved = host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyHostToDevice, s, &e);
-    if (e == cudaSuccess) {
-        st = tri_inv_ex(uplo, diag, n, buf, ldd, dtype, need ? buf + mat : nullptr, need, nullptr, stream);
-        if (st == TRI_OK)
-            moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+    int64_t moved = 0;
+    if (dtype == TRI_F32_MIXED && c.device >= 0 && c.device < 64) {
+        // copies by parts on the copy stream, the inverse waiting for each part where needed
+        std::lock_guard<std::mutex> lk(g_feed_mu);
+        HostFeed &f = g_feed[c.device];
+        if (!f.s) {
+            bool ok = cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+            for (cudaEvent_t &ev : f.ready)
+                ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) e = cudaErrorUnknown;
+        }
+        int parts = 0;
+        if (e == cudaSuccess &&
+            (e = cudaEventRecord(f.fork, s)) == cudaSuccess &&   // after the buffer's allocation
+            (e = cudaStreamWaitEvent(f.s, f.fork, 0)) == cudaSuccess)
+            moved = host_block_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, f, &parts, &e);
+        if (e == cudaSuccess) {
+            const InputFeed feed{f.ready, parts};
+            if ((st = info_begin(c, nullptr)) == TRI_OK)
+                st = info_end(c, nullptr,
+                              run_mixed_fed(c, upper, diag == TRI_UNIT, n, (float *)buf, ldd, need ? buf + mat : nullptr,
+                                            &feed));
+            // every part is in before the result goes back and the buffer is freed
+            if (parts > 0 && cudaStreamWaitEvent(s, f.ready[parts - 1], 0) != cudaSuccess) e = cudaErrorUnknown;
+            if (st == TRI_OK && e == cudaSuccess)
+                moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+        }
+    } else {
+        moved = host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyHostToDevice, s, &e);
+        if (e == cudaSuccess) {
+            st = tri_inv_ex(uplo, diag, n, buf, ldd, dtype, need ? buf + mat : nullptr, need, nullptr, stream);
+            if (st == TRI_OK)
+                moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+        }
     }
     const cudaError_t ef = cudaFreeAsync(buf, s);
     const cudaError_t es2 = cudaStreamSynchronize(s);

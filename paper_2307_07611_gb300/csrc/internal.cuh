@@ -77,6 +77,18 @@ cudaError_t launch_trmm_level(const Ctx &c, tri_dtype dt, bool trans, bool unit,
                               int64_t n, void *a, int64_t lda, int64_t h, void *w,
                               int64_t batch = 1, int64_t bstride = 0);
 
+// Copies in flight that write parts of the input matrix of the mixed path (tri_inv_host):
+// the inverse waits for each part only where it first reads it.  ready[0]: the diagonal
+// 256-blocks and the B blocks of the first mixed_head_levels() split levels; ready[1 + k]:
+// the B blocks of level mixed_head_levels() + k (half-size 256 * 2^level).
+struct InputFeed {
+    const cudaEvent_t *ready;
+    int count;
+};
+int mixed_head_levels();
+tri_status run_mixed_fed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws,
+                         const InputFeed *feed);
+
 // Number of active pairs at split half-size h.
 inline int64_t level_pairs(int64_t n, int64_t h) {
     return n > h ? (n - h + 2 * h - 1) / (2 * h) : 0;

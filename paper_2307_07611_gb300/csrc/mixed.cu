@@ -52,6 +52,7 @@ cudaError_t launch_diag_blocks(const Ctx &c, bool trans, bool unit, int64_t n, f
 struct SideStream {
     cudaStream_t s = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+    cudaEvent_t lev[24] = {};   // per split level, when the input arrives by level (InputFeed)
 };
 std::mutex g_side_mu;
 SideStream g_side[64];
@@ -65,6 +66,8 @@ bool side_stream(int dev, SideStream **out) {
         if (cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) != cudaSuccess) return false;
         if (cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming) != cudaSuccess) return false;
         if (cudaEventCreateWithFlags(&ss.join2, cudaEventDisableTiming) != cudaSuccess) return false;
+        for (cudaEvent_t &e : ss.lev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
     }
     *out = &ss;
     return true;
@@ -468,7 +471,7 @@ namespace {
 // index0 >= 0: matrices of a batch starting at index index0 (zero pivots report the
 // matrix index); -1: a single matrix (zero pivots report the row).
 tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, int64_t stride,
-                           int64_t batch, int64_t index0, void *ws) {
+                           int64_t batch, int64_t index0, void *ws, const InputFeed *feed = nullptr) {
     const Layout L = layout(n, batch);
     uint8_t *base = (uint8_t *)ws;
     const size_t g = L.plane * (size_t)batch;   // bytes of one plane group
@@ -509,6 +512,9 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     SideStream *ss = nullptr;
     std::unique_lock<std::mutex> side_lock(g_side_mu);
     if (!side_stream(c.device, &ss)) return TRI_ERR_CUDA;
+    // input arriving by parts: the head waits for the diagonal blocks and the first levels
+    if (feed && feed->count > 0 && cudaStreamWaitEvent(c.stream, feed->ready[0], 0) != cudaSuccess)
+        return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->fork, c.stream) != cudaSuccess || cudaStreamWaitEvent(ss->s, ss->fork, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
     // The diagonal-block kernel goes first: each of its CTAs needs a whole SM's shared
@@ -530,21 +536,40 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         return TRI_ERR_CUDA;
     if (cudaEventRecord(ss->join, ss->s) != cudaSuccess || cudaStreamWaitEvent(c.stream, ss->join, 0) != cudaSuccess)
         return TRI_ERR_CUDA;
-    if (rest) {
+    // Input by parts (feed): one split launch per later level, each after its part arrives,
+    // each with a join event of its own; otherwise one launch for all later levels.
+    const bool by_level = rest && feed && feed->count >= 1 + nlevels - kHeadLevels &&
+                          nlevels - kHeadLevels <= (int)(sizeof(ss->lev) / sizeof(ss->lev[0]));
+    if (rest && by_level) {
+        for (int l = kHeadLevels; l < nlevels; ++l)
+            if (cudaStreamWaitEvent(ss->s, feed->ready[1 + l - kHeadLevels], 0) != cudaSuccess ||
+                launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride,
+                                    ps, l, l) != cudaSuccess ||
+                cudaEventRecord(ss->lev[l - kHeadLevels], ss->s) != cudaSuccess)
+                return TRI_ERR_CUDA;
+    } else if (rest) {
+        if (feed)   // parts arrive in order: the last one completes the input
+            for (int k = 1; k < feed->count; ++k)
+                if (cudaStreamWaitEvent(ss->s, feed->ready[k], 0) != cudaSuccess) return TRI_ERR_CUDA;
         if (launch_split_planes(cs, trans, unit, false, n, a, lda, T[0], T[1], T[2], L.ldp, true, batch, stride, ps,
                                 kHeadLevels, 62) != cudaSuccess ||
             cudaEventRecord(ss->join2, ss->s) != cudaSuccess)
             return TRI_ERR_CUDA;
     }
-    // the main stream's wait for the rest of the planes (before level kHeadLevels)
-    bool rest_joined = !rest;
-    auto join_rest = [&]() -> bool {
-        if (rest_joined) return true;
-        rest_joined = true;
-        const bool ok = cudaStreamWaitEvent(c.stream, ss->join2, 0) == cudaSuccess;
-        side_lock.unlock();
+    // The main stream's waits for the planes of level l >= kHeadLevels, enqueued before
+    // the level's first product; the side stream's lock is held until the last one.
+    int joined = rest ? kHeadLevels : nlevels;   // levels whose planes the main stream has
+    auto join_level = [&](int l) -> bool {
+        bool ok = true;
+        while (joined <= l && joined < nlevels) {
+            if (by_level) ok = ok && cudaStreamWaitEvent(c.stream, ss->lev[joined - kHeadLevels], 0) == cudaSuccess;
+            else if (joined == kHeadLevels) ok = ok && cudaStreamWaitEvent(c.stream, ss->join2, 0) == cudaSuccess;
+            ++joined;
+        }
+        if (joined >= nlevels && side_lock.owns_lock()) side_lock.unlock();
         return ok;
     };
+    auto join_rest = [&]() -> bool { return join_level(nlevels); };
     if (!rest) side_lock.unlock();
 
     if (graph) {
@@ -608,9 +633,10 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     int lvl = 0;
     for (int64_t h = hfirst; h < n; h *= 2, ++lvl) {
         const int64_t P = level_pairs(n, h);
-        int name = 0;   // trace name index: log2(h / 256)
-        while ((kDiag << name) < h && name < 7) ++name;
-        if (name >= kHeadLevels && !join_rest()) return TRI_ERR_CUDA;
+        int lv = 0;   // split level: log2(h / 256)
+        while ((kDiag << lv) < h) ++lv;
+        const int name = std::min(lv, 7);   // trace name index
+        if (lv >= kHeadLevels && !join_level(lv)) return TRI_ERR_CUDA;
         const tc::Plane wp[3] = {pl(W[0], h, P * h, h), pl(W[1], h, P * h, h), pl(W[2], h, P * h, h)};
         tc::Epi ew{nullptr, 0, W[0], W[1], direct ? W[2] : nullptr, h, h, P * h};
         ew.os = ps;
@@ -655,6 +681,20 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
 tri_status run_mixed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws) {
     if (n <= kDiag) return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
     return run_mixed_chunk(c, trans, unit, n, a, lda, 0, 1, -1, ws);
+}
+
+int mixed_head_levels() { return split_head_levels(); }
+
+// run_mixed with the input arriving by parts (see InputFeed): every part's event is waited
+// for before anything reads that part.
+tri_status run_mixed_fed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws,
+                         const InputFeed *feed) {
+    if (n <= kDiag) {
+        for (int k = 0; feed && k < feed->count; ++k)
+            if (cudaStreamWaitEvent(c.stream, feed->ready[k], 0) != cudaSuccess) return TRI_ERR_CUDA;
+        return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
+    }
+    return run_mixed_chunk(c, trans, unit, n, a, lda, 0, 1, -1, ws, feed);
 }
 
 // `batch` matrices `stride` elements apart (n > 256), in chunks whose planes fit the

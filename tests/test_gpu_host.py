@@ -4,7 +4,8 @@ products add split-k partial sums atomically, so TRI_F64 agrees to a few units i
 place), only the referenced triangle of
 the host buffer changes (the other triangle holds NaN, padding rows and a tail guard hold
 a canary), pinned and pageable host memory both work, and the reported byte count is the
-triangle's panels in both directions."""
+triangle's panels in both directions (the mixed path sends the blocks of the recursive split
+instead, in the order the inverse first reads them)."""
 import numpy as np
 import pytest
 
@@ -33,9 +34,25 @@ def panel_bytes(n, lower, es):
     return 2 * total
 
 
+def block_bytes(n, es):
+    """Host-to-device bytes of the mixed path, which sends the matrix in the blocks of the
+    recursive split: the 256 x 256 diagonal squares, then every pair's B block (hc x h) of
+    every level h = 256, 512, ... < n."""
+    total = sum(min(256, n - d0) ** 2 for d0 in range(0, n, 256))
+    h = 256
+    while h < n:
+        q = 0
+        while 2 * q * h + h < n:
+            c0 = 2 * q * h + h
+            total += min(h, n - c0) * h
+            q += 1
+        h *= 2
+    return total * es
+
+
 @pytest.mark.parametrize("dt", ["f32", "f64", "mixed"])
 @pytest.mark.parametrize("lower,unit", [(True, False), (False, False), (True, True)])
-@pytest.mark.parametrize("n,pinned", [(300, True), (1000, False), (777, True)])
+@pytest.mark.parametrize("n,pinned", [(300, True), (1000, False), (777, True), (2500, True)])
 def test_host_matches_device(lib, dt, lower, unit, n, pinned):
     t = inputs.tri_lower(n, seed=n + 7, law="uniform")
     if not lower:
@@ -55,7 +72,10 @@ def test_host_matches_device(lib, dt, lower, unit, n, pinned):
     assert st == lib.TRI_OK and lib.tri_get_info()[0] == lib.TRI_OK
     out = buf.numpy()
     check_untouched(host0, out, n, ld, lower, unit)
-    assert moved == panel_bytes(n, lower, np_dt().itemsize)
+    if dt == "mixed":   # blocks in, panels out
+        assert moved == block_bytes(n, 4) + panel_bytes(n, lower, 4) // 2
+    else:
+        assert moved == panel_bytes(n, lower, np_dt().itemsize)
     x = from_colmajor_buffer(out, n, ld)
     x = np.tril(x) if lower else np.triu(x)
     if unit:
