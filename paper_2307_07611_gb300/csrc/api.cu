@@ -329,12 +329,15 @@ tri_status tri_inv(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_t lda
 
 // Host-memory form: the referenced triangle travels in 256-column panels (one 2-D copy
 // each), so about half of the n x n matrix crosses the host link in each direction.
+// Columns [jlo, jhi) only (jlo a multiple of 256) when given.
 static int64_t host_panel_copies(bool upper, int64_t n, uint8_t *dev, int64_t ldd, uint8_t *host, int64_t ldh,
-                                 size_t es, cudaMemcpyKind kind, cudaStream_t s, cudaError_t *err) {
+                                 size_t es, cudaMemcpyKind kind, cudaStream_t s, cudaError_t *err, int64_t jlo = 0,
+                                 int64_t jhi = -1) {
     constexpr int64_t kPanel = 256;
     int64_t bytes = 0;
-    for (int64_t j0 = 0; j0 < n && *err == cudaSuccess; j0 += kPanel) {
-        const int64_t cols = std::min(kPanel, n - j0);
+    if (jhi < 0 || jhi > n) jhi = n;
+    for (int64_t j0 = jlo; j0 < jhi && *err == cudaSuccess; j0 += kPanel) {
+        const int64_t cols = std::min(kPanel, jhi - j0);
         const int64_t r0 = upper ? 0 : j0, rows = upper ? j0 + cols : n - j0;
         uint8_t *d = dev + ((size_t)j0 * ldd + r0) * es, *h = host + ((size_t)j0 * ldh + r0) * es;
         *err = kind == cudaMemcpyHostToDevice
@@ -352,8 +355,9 @@ static int64_t host_panel_copies(bool upper, int64_t n, uint8_t *dev, int64_t ld
 // the rest is still in flight (run_mixed_fed).
 struct HostFeed {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr;
+    cudaEvent_t fork = nullptr, back = nullptr;
     cudaEvent_t ready[26] = {};
+    cudaEvent_t done[8] = {};
 };
 std::mutex g_feed_mu;
 HostFeed g_feed[64];
@@ -423,8 +427,11 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
         HostFeed &f = g_feed[c.device];
         if (!f.s) {
             bool ok = cudaStreamCreateWithFlags(&f.s, cudaStreamNonBlocking) == cudaSuccess &&
-                      cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+                      cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&f.back, cudaEventDisableTiming) == cudaSuccess;
             for (cudaEvent_t &ev : f.ready)
+                ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            for (cudaEvent_t &ev : f.done)
                 ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
             if (!ok) e = cudaErrorUnknown;
         }
@@ -435,14 +442,31 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
             moved = host_block_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, f, &parts, &e);
         if (e == cudaSuccess) {
             const InputFeed feed{f.ready, parts};
+            // the result goes back by column groups, each as soon as the update has
+            // finished its columns, on the copy stream beside the later groups' updates
+            // (lower storage only: for an upper matrix the columns of the lower view are
+            // stored rows, which do not map onto panels of the stored triangle)
+            OutputDrain drain{upper ? 1 : 4, f.done, 0, {}, {}};
             if ((st = info_begin(c, nullptr)) == TRI_OK)
                 st = info_end(c, nullptr,
                               run_mixed_fed(c, upper, diag == TRI_UNIT, n, (float *)buf, ldd, need ? buf + mat : nullptr,
-                                            &feed));
+                                            &feed, &drain));
             // every part is in before the result goes back and the buffer is freed
             if (parts > 0 && cudaStreamWaitEvent(s, f.ready[parts - 1], 0) != cudaSuccess) e = cudaErrorUnknown;
-            if (st == TRI_OK && e == cudaSuccess)
-                moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+            if (st == TRI_OK && e == cudaSuccess) {
+                if (drain.got > 0) {
+                    for (int g = 0; g < drain.got && e == cudaSuccess; ++g) {
+                        if ((e = cudaStreamWaitEvent(f.s, f.done[g], 0)) != cudaSuccess) break;
+                        moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost,
+                                                   f.s, &e, drain.col_lo[g], drain.col_hi[g]);
+                    }
+                    // the stream sees the copies out before it frees the buffer and returns
+                    if (e == cudaSuccess && (e = cudaEventRecord(f.back, f.s)) == cudaSuccess)
+                        e = cudaStreamWaitEvent(s, f.back, 0);
+                } else {
+                    moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
+                }
+            }
         }
     } else {
         moved = host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyHostToDevice, s, &e);

@@ -85,9 +85,19 @@ struct InputFeed {
     const cudaEvent_t *ready;
     int count;
 };
+// Where the result of the mixed path is final early (tri_inv_host): with groups > 1 the
+// Newton-Schulz update runs in column groups from the right, and done[g] is recorded on
+// the stream after group g, whose columns [col_lo[g], col_hi[g]) (multiples of 256) are
+// then final.  The callee sets `got` (0: no groups, the result is final at the end).
+struct OutputDrain {
+    int groups;                  // wanted (at most 8)
+    const cudaEvent_t *done;     // groups events
+    int got;
+    int64_t col_lo[8], col_hi[8];
+};
 int mixed_head_levels();
 tri_status run_mixed_fed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws,
-                         const InputFeed *feed);
+                         const InputFeed *feed, OutputDrain *drain = nullptr);
 
 // Number of active pairs at split half-size h.
 inline int64_t level_pairs(int64_t n, int64_t h) {

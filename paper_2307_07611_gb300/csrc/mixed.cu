@@ -190,6 +190,8 @@ struct Plan {
     int *d_off = nullptr;
     std::vector<Launch> w, x21;   // per tc level (the levels after the merged ones)
     Launch res{}, upd{};
+    std::vector<Launch> upd_parts;     // the update in column groups, rightmost first
+    std::vector<int64_t> upd_lo, upd_hi;
     Launch lvl{};                 // merged low levels (MODE_LVL), if merged_levels > 0
     int merged_levels = 0;        // h = 256 .. 256 * 2^(merged_levels - 1)
     int64_t wld = 0, wcols = 0;   // W layout of the merged levels: wld x wcols, ld = wld
@@ -233,17 +235,19 @@ bool use_merged_levels() {
 }
 
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int64_t, int64_t, int, int>, Plan> g_plans;
+std::map<std::tuple<int, int64_t, int64_t, int, int, int>, Plan> g_plans;
 
 // Tile lists of every product for `batch` matrices of order n (each product's tiles of
 // all matrices in one longest-first schedule).  recipe TRI_RECIPE_DIRECT: the level
 // products take six terms (longest-first costs follow) and there is no Newton-Schulz step.
-tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64_t batch, int recipe, Plan **out) {
+tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64_t batch, int recipe, Plan **out,
+                      int ugroups = 1) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     const bool direct = recipe == TRI_RECIPE_DIRECT;
     const int lterms = direct ? 6 : 3;
     if (direct) pm = 0;
-    auto key = std::make_tuple(dev, n, batch, recipe, pm);
+    if (direct || ugroups < 2) ugroups = 1;
+    auto key = std::make_tuple(dev, n, batch, recipe, pm, ugroups);
     auto it = g_plans.find(key);
     if (it != g_plans.end()) {
         *out = &it->second;
@@ -427,6 +431,27 @@ tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64
         add(nullptr, pass == 0 ? &p.res : &p.upd, from, (pass == 0 ? 6.0 : 1.0) * lower_prod,
             pass == 0 ? 6 : 1, tc::BN, pp);
     }
+    if (!direct && ugroups > 1) {
+        // The update again, in ugroups column groups (rightmost first): tile columns
+        // [tc0, tc1) of 256; flops 2 (i - j + 1) for each lower entry (i, j) of the group.
+        const int64_t tcn = cdiv(n, tc::BN);
+        for (int g = ugroups - 1; g >= 0; --g) {
+            const int64_t tc0 = tcn * g / ugroups, tc1 = tcn * (g + 1) / ugroups;
+            if (tc1 <= tc0) continue;
+            const size_t from = v.size();
+            for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
+                const int64_t kend = std::min((tm + 1) * tc::BM, n);
+                for (int64_t tn = tc0; tn < tc1 && tn * tc::BN < kend; ++tn)
+                    v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
+                                         (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
+            }
+            double fl = 0.0;
+            for (int64_t j = tc0 * tc::BN; j < std::min(tc1 * tc::BN, n); ++j) fl += (double)(n - j) * (n - j + 1);
+            add(&p.upd_parts, nullptr, from, fl, 1);
+            p.upd_lo.push_back(tc0 * tc::BN);
+            p.upd_hi.push_back(std::min(tc1 * tc::BN, n));
+        }
+    }
     if (!v.empty()) {
         const size_t tb = v.size() * sizeof(tc::Tile), ob = offs.size() * sizeof(int);
         uint8_t *d = nullptr;
@@ -471,7 +496,8 @@ namespace {
 // index0 >= 0: matrices of a batch starting at index index0 (zero pivots report the
 // matrix index); -1: a single matrix (zero pivots report the row).
 tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, int64_t stride,
-                           int64_t batch, int64_t index0, void *ws, const InputFeed *feed = nullptr) {
+                           int64_t batch, int64_t index0, void *ws, const InputFeed *feed = nullptr,
+                           OutputDrain *drain = nullptr) {
     const Layout L = layout(n, batch);
     uint8_t *base = (uint8_t *)ws;
     const size_t g = L.plane * (size_t)batch;   // bytes of one plane group
@@ -492,7 +518,8 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     Plan *plan = nullptr;
     tri_status st = graph ? tc::graph_plan(c.device, c.sm_count, n, &gplan)
                           : build_plan(c.device, c.sm_count, c.pairs ? tc::pair_lists(c) : 0, c.pairs, n, batch,
-                                       c.recipe, &plan);
+                                       c.recipe, &plan, drain ? std::min(drain->groups, 8) : 1);
+    if (drain) drain->got = 0;
     if (st != TRI_OK) return st;
     // dependency counters of the merged low levels start at zero
     int *cnt = (int *)(base + L.off_c);
@@ -669,6 +696,21 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
     const tc::Terms one{1, {0}, {0}};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
     eu.xs = stride;
+    if (drain && !plan->upd_parts.empty()) {
+        // column groups from the right; each group's columns are final after its launch
+        const int np = (int)plan->upd_parts.size();
+        for (int g = 0; g < np; ++g) {
+            const Launch &lu = plan->upd_parts[g];
+            if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + lu.first,
+                              plan->d_off + lu.off_first, lu.ctas, eu, lu.flops, "tc_gemm:upd", tc::BN) != cudaSuccess ||
+                cudaEventRecord(drain->done[g], c.stream) != cudaSuccess)
+                return TRI_ERR_CUDA;
+            drain->col_lo[g] = plan->upd_lo[g];
+            drain->col_hi[g] = plan->upd_hi[g];
+        }
+        drain->got = np;
+        return TRI_OK;
+    }
     if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + plan->upd.first,
                       plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd", tc::BN,
                       plan->upd.pair) != cudaSuccess)
@@ -688,13 +730,14 @@ int mixed_head_levels() { return split_head_levels(); }
 // run_mixed with the input arriving by parts (see InputFeed): every part's event is waited
 // for before anything reads that part.
 tri_status run_mixed_fed(const Ctx &c, bool trans, bool unit, int64_t n, float *a, int64_t lda, void *ws,
-                         const InputFeed *feed) {
+                         const InputFeed *feed, OutputDrain *drain) {
+    if (drain) drain->got = 0;
     if (n <= kDiag) {
         for (int k = 0; feed && k < feed->count; ++k)
             if (cudaStreamWaitEvent(c.stream, feed->ready[k], 0) != cudaSuccess) return TRI_ERR_CUDA;
         return run_plain_levels(c, TRI_F32, trans, unit, n, a, lda, ws, n);
     }
-    return run_mixed_chunk(c, trans, unit, n, a, lda, 0, 1, -1, ws, feed);
+    return run_mixed_chunk(c, trans, unit, n, a, lda, 0, 1, -1, ws, feed, drain);
 }
 
 // `batch` matrices `stride` elements apart (n > 256), in chunks whose planes fit the
