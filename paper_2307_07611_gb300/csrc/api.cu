@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -446,7 +447,12 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
             // finished its columns, on the copy stream beside the later groups' updates
             // (lower storage only: for an upper matrix the columns of the lower view are
             // stored rows, which do not map onto panels of the stored triangle)
-            OutputDrain drain{upper ? 1 : 4, f.done, 0, {}, {}};
+            static const int kGroups = [] {   // TRI_HOST_GROUPS (1..8) overrides, read once
+                const char *ev = std::getenv("TRI_HOST_GROUPS");
+                const int v = ev ? std::atoi(ev) : 4;
+                return v >= 1 && v <= 8 ? v : 4;
+            }();
+            OutputDrain drain{upper ? 1 : kGroups, f.done, 0, {}, {}};
             if ((st = info_begin(c, nullptr)) == TRI_OK)
                 st = info_end(c, nullptr,
                               run_mixed_fed(c, upper, diag == TRI_UNIT, n, (float *)buf, ldd, need ? buf + mat : nullptr,
