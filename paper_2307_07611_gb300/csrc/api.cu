@@ -387,10 +387,13 @@ static int64_t host_block_copies(bool upper, int64_t n, uint8_t *dev, int64_t ld
         }
     };
     int k = 0;
-    for (int64_t d0 = 0; d0 < n; d0 += kDiagB) copy(d0, std::min(kDiagB, n - d0), d0, std::min(kDiagB, n - d0));
-    int l = 0;
-    int64_t h = kDiagB;
-    for (; h < n && l < head; h *= 2, ++l) level_blocks(h);
+    // the first part, as 256-column panels down to the end of each band of 256 * 2^head
+    // rows: the diagonal squares and the B blocks of the first `head` levels, in one copy per
+    // panel
+    const int64_t band = kDiagB << head;
+    for (int64_t j0 = 0; j0 < n; j0 += kDiagB)
+        copy(j0, std::min(n, (j0 / band + 1) * band) - j0, j0, std::min(kDiagB, n - j0));
+    int64_t h = kDiagB << head;
     if (*err == cudaSuccess) *err = cudaEventRecord(f.ready[k++], f.s);
     for (; h < n && k < 26; h *= 2) {
         level_blocks(h);
