@@ -338,9 +338,9 @@ TRI_API tri_status tri_inv_combrit(tri_uplo uplo, tri_diag diag, int64_t n, void
  * triangle instead as the blocks of the recursive split (the 256 x 256 diagonal squares,
  * then each level's off-diagonal blocks), on a copy stream of the library's, in the order
  * the inverse first reads them: the inverse starts on the first blocks while the rest is
- * in flight; for a lower matrix the result returns in four column groups, each as soon as
- * the last product has finished its columns, beside the products of the others (the
- * result is the same either way).  Device memory for the matrix
+ * in flight; for a lower matrix the Newton-Schulz products run in four column groups and
+ * each group's columns return as soon as they are final, beside the products of the
+ * others (the result is the same either way).  Device memory for the matrix
  * and the workspace comes from the stream-ordered pool and is released before return.
  * Synchronises `stream` before returning (the host matrix holds the result on return).
  * Page-locked host memory gives full link bandwidth; pageable memory also works.

@@ -190,7 +190,7 @@ struct Plan {
     int *d_off = nullptr;
     std::vector<Launch> w, x21;   // per tc level (the levels after the merged ones)
     Launch res{}, upd{};
-    std::vector<Launch> upd_parts;     // the update in column groups, rightmost first
+    std::vector<Launch> res_parts, upd_parts;   // both products in column groups, rightmost first
     std::vector<int64_t> upd_lo, upd_hi;
     Launch lvl{};                 // merged low levels (MODE_LVL), if merged_levels > 0
     int merged_levels = 0;        // h = 256 .. 256 * 2^(merged_levels - 1)
@@ -432,22 +432,28 @@ tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64
             pass == 0 ? 6 : 1, tc::BN, pp);
     }
     if (!direct && ugroups > 1) {
-        // The update again, in ugroups column groups (rightmost first): tile columns
-        // [tc0, tc1) of 256; flops 2 (i - j + 1) for each lower entry (i, j) of the group.
+        // Both Newton-Schulz products again, in ugroups column groups (rightmost first):
+        // tile columns [tc0, tc1) of 256.  Columns j of X R need only columns j of R, and R
+        // reads only planes that the update does not write, so group by group the residual
+        // and then the update finish those columns of the result.  Flops 2 (i - j + 1) per
+        // term for each lower entry (i, j) of the group.
         const int64_t tcn = cdiv(n, tc::BN);
         for (int g = ugroups - 1; g >= 0; --g) {
             const int64_t tc0 = tcn * g / ugroups, tc1 = tcn * (g + 1) / ugroups;
             if (tc1 <= tc0) continue;
-            const size_t from = v.size();
-            for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
-                const int64_t kend = std::min((tm + 1) * tc::BM, n);
-                for (int64_t tn = tc0; tn < tc1 && tn * tc::BN < kend; ++tn)
-                    v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
-                                         (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
-            }
             double fl = 0.0;
             for (int64_t j = tc0 * tc::BN; j < std::min(tc1 * tc::BN, n); ++j) fl += (double)(n - j) * (n - j + 1);
-            add(&p.upd_parts, nullptr, from, fl, 1);
+            for (int pass = 0; pass < 2; ++pass) {
+                const size_t from = v.size();
+                for (int64_t tm = 0; tm < cdiv(n, tc::BM); ++tm) {
+                    const int64_t kend = std::min((tm + 1) * tc::BM, n);
+                    for (int64_t tn = tc0; tn < tc1 && tn * tc::BN < kend; ++tn)
+                        v.push_back(tc::Tile{(int)(tm * tc::BM), 0, 0, (int)(tn * tc::BN), (int)(tn * tc::BN / tc::BK),
+                                             (int)cdiv(kend, tc::BK), (int)(tm * tc::BM), (int)(tn * tc::BN)});
+                }
+                add(pass == 0 ? &p.res_parts : &p.upd_parts, nullptr, from, (pass == 0 ? 6.0 : 1.0) * fl,
+                    pass == 0 ? 6 : 1);
+            }
             p.upd_lo.push_back(tc0 * tc::BN);
             p.upd_hi.push_back(std::min(tc1 * tc::BN, n));
         }
@@ -688,21 +694,20 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         er.skip = gflags;
         er.skip_n = (int)((n + kDiag - 1) / kDiag);
     }
-    if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
-                      plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res", tc::BN,
-                      plan->res.pair) != cudaSuccess)
-        return TRI_ERR_CUDA;
     const tc::Plane rp[1] = {pl(R[0], n, n, L.ldp)};
     const tc::Terms one{1, {0}, {0}};
     tc::Epi eu{a, lda, nullptr, nullptr, nullptr, 0, n, n};
     eu.xs = stride;
     if (drain && !plan->upd_parts.empty()) {
-        // column groups from the right; each group's columns are final after its launch
+        // column groups from the right: residual then update of the group; its columns of
+        // the result are final after the update
         const int np = (int)plan->upd_parts.size();
         for (int g = 0; g < np; ++g) {
-            const Launch &lu = plan->upd_parts[g];
-            if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + lu.first,
-                              plan->d_off + lu.off_first, lu.ctas, eu, lu.flops, "tc_gemm:upd", tc::BN) != cudaSuccess ||
+            const Launch &lr = plan->res_parts[g], &lu = plan->upd_parts[g];
+            if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + lr.first,
+                              plan->d_off + lr.off_first, lr.ctas, er, lr.flops, "tc_gemm:res") != cudaSuccess ||
+                tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + lu.first,
+                              plan->d_off + lu.off_first, lu.ctas, eu, lu.flops, "tc_gemm:upd") != cudaSuccess ||
                 cudaEventRecord(drain->done[g], c.stream) != cudaSuccess)
                 return TRI_ERR_CUDA;
             drain->col_lo[g] = plan->upd_lo[g];
@@ -711,6 +716,10 @@ tri_status run_mixed_chunk(const Ctx &c, bool trans, bool unit, int64_t n, float
         drain->got = np;
         return TRI_OK;
     }
+    if (tc::launch_tc(c, tc::MODE_RES, trans, unit, tp, 3, xp, 3, six, plan->d_tiles + plan->res.first,
+                      plan->d_off + plan->res.off_first, plan->res.ctas, er, plan->res.flops, "tc_gemm:res", tc::BN,
+                      plan->res.pair) != cudaSuccess)
+        return TRI_ERR_CUDA;
     if (tc::launch_tc(c, tc::MODE_UPD, trans, unit, xp, 1, rp, 1, one, plan->d_tiles + plan->upd.first,
                       plan->d_off + plan->upd.off_first, plan->upd.ctas, eu, plan->upd.flops, "tc_gemm:upd", tc::BN,
                       plan->upd.pair) != cudaSuccess)
