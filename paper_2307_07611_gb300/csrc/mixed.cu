@@ -438,8 +438,33 @@ tri_status build_plan(int dev, int sm_count, int pairs, int pm, int64_t n, int64
         // and then the update finish those columns of the result.  Flops 2 (i - j + 1) per
         // term for each lower entry (i, j) of the group.
         const int64_t tcn = cdiv(n, tc::BN);
+        // group boundaries in tile columns: for four groups at 1/8, 3/8 and 5/8 of the
+        // columns (the leftmost group, whose copy back is not overlapped, holds the longest
+        // columns; measured at n = 8192: 2.35 ms end to end against 2.51 for equal widths),
+        // else equal widths; TRI_HOST_BOUNDS="f1,f2,..." (ugroups - 1 increasing fractions of
+        // n) overrides
+        std::vector<int64_t> bnd(ugroups + 1);
+        for (int g = 0; g <= ugroups; ++g) bnd[g] = tcn * g / ugroups;
+        if (ugroups == 4) {
+            bnd[1] = (tcn + 4) / 8;
+            bnd[2] = std::max(bnd[1], (3 * tcn + 4) / 8);
+            bnd[3] = std::max(bnd[2], (5 * tcn + 4) / 8);
+        }
+        if (const char *e = std::getenv("TRI_HOST_BOUNDS")) {
+            std::vector<double> f;
+            for (const char *q = e; *q;) {
+                char *end = nullptr;
+                const double x = std::strtod(q, &end);
+                if (end == q) break;
+                f.push_back(x);
+                q = *end == ',' ? end + 1 : end;
+            }
+            if ((int)f.size() == ugroups - 1)
+                for (int g = 1; g < ugroups; ++g)
+                    bnd[g] = std::max(bnd[g - 1], std::min(tcn, (int64_t)(f[g - 1] * (double)tcn + 0.5)));
+        }
         for (int g = ugroups - 1; g >= 0; --g) {
-            const int64_t tc0 = tcn * g / ugroups, tc1 = tcn * (g + 1) / ugroups;
+            const int64_t tc0 = bnd[g], tc1 = bnd[g + 1];
             if (tc1 <= tc0) continue;
             double fl = 0.0;
             for (int64_t j = tc0 * tc::BN; j < std::min(tc1 * tc::BN, n); ++j) fl += (double)(n - j) * (n - j + 1);
