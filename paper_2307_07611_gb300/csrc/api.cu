@@ -469,9 +469,11 @@ tri_status tri_inv_host(tri_uplo uplo, tri_diag diag, int64_t n, void *a, int64_
                         moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost,
                                                    f.s, &e, drain.col_lo[g], drain.col_hi[g]);
                     }
-                    // the stream sees the copies out before it frees the buffer and returns
-                    if (e == cudaSuccess && (e = cudaEventRecord(f.back, f.s)) == cudaSuccess)
-                        e = cudaStreamWaitEvent(s, f.back, 0);
+                    // the stream sees the copies out (also those queued before a failed one)
+                    // before it frees the buffer and returns
+                    const cudaError_t eb = cudaEventRecord(f.back, f.s);
+                    const cudaError_t ew = eb == cudaSuccess ? cudaStreamWaitEvent(s, f.back, 0) : eb;
+                    if (e == cudaSuccess) e = ew;
                 } else {
                     moved += host_panel_copies(upper, n, buf, ldd, (uint8_t *)a, lda, es, cudaMemcpyDeviceToHost, s, &e);
                 }
